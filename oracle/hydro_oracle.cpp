@@ -1,0 +1,688 @@
+/*
+ * ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct FP64 CPU implementation of one unsplit
+ * PPM Godunov update of the 3D Euler equations for an ideal gamma-law gas
+ * on a box with ghost zones.  Only the tests, the smoke check and the timed
+ * CPU baseline of the benchmark may call it.  It shares no code, header,
+ * table or constant with the CUDA library, and never runs on its behalf.
+ *
+ * What the paper fixes.  §3 ("Porting to GPUs") describes the core stencil:
+ * limited slopes from neighbouring zones, then a polynomial reconstruction of
+ * the fluid state.  §4 says the hydro is close to the one in Cholla, and §4.A
+ * that the blast-wave test couples hydro and equation of state.  The paper
+ * gives no formulas, so each stage below restates the published method it
+ * names (Colella & Woodward 1984 = CW84; Colella 1990 and Saltzman 1994 for
+ * the corner-transport-upwind (CTU) corrections; Toro, Spruce & Speares 1994
+ * and Batten et al. 1997 for HLLC; Miller & Colella 2002 for characteristic
+ * tracing).  The constants and readings listed here are choices:
+ *
+ *   R1  floors: small_dens = small_pres = 1e-12, applied to primitive copies only.
+ *   R2  flattening (CW84 §4): eps = 0.33, omega1 = 0.75, omega2 = 10;
+ *       f_i = max(ft_i, ft_{i-s}), s = sign(p_{i+1}-p_{i-1}) (+1 on a tie);
+ *       one coefficient per zone = max over the three directions.
+ *   R3  PPM (CW84 eqs. 1.6-1.10): van Leer limited slopes, 4th-order
+ *       interface values, CW84 monotonicity limiter, then flattening blend.
+ *   R4  tracing: reference state = integral of the parabola under the fastest
+ *       wave moving toward the edge (zone value if none), characteristic
+ *       projection with zone-centred rho and c; waves with lambda == 0 excluded.
+ *   R5  HLLC with Roe-averaged (Batten) wave-speed bounds, Davis bounds when
+ *       the Roe sound speed squared is <= 0; S* == 0 takes the left star state.
+ *   R6  3D CTU: stage 1 corrections with factor dt/(3 dx_e), stage 2 with
+ *       dt/(2 dx_e); corrections in conserved variables; a corrected state
+ *       with rho <= 0 or p <= 0 reverts to the uncorrected one.
+ *   R7  dt = cfl * min over interior zones and directions of dx_d/(|u_d|+c),
+ *       computed from the state before the step.
+ *   R8  ghost fill in the order x, y, z (later directions span the earlier
+ *       directions' ghosts, so edges and corners are filled).
+ *
+ * Layout: every field is a [k][j][i] array over the ghosted box
+ * (nx+2g)(ny+2g)(nz+2g), i fastest, no padding.  Conserved state
+ * U = (rho, rho u, rho v, rho w, E); primitive q = (rho, u, v, w, p).
+ *
+ * Build with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+typedef struct {
+  int nx, ny, nz;   /* interior zones per axis */
+  int ng;           /* ghost zones per side */
+  double dx[3];     /* zone widths */
+  double gamma;     /* ratio of specific heats */
+  double cfl;       /* Courant number */
+  int bc[6];        /* xlo,xhi,ylo,yhi,zlo,zhi: 0 periodic, 1 outflow, 2 reflect */
+} ob_box;
+}
+
+enum { OB_PERIODIC = 0, OB_OUTFLOW = 1, OB_REFLECT = 2 };
+
+static const double SMALL_DENS = 1e-12;
+static const double SMALL_PRES = 1e-12;
+static const double FLAT_EPS = 0.33;
+static const double FLAT_OMEGA1 = 0.75;
+static const double FLAT_OMEGA2 = 10.0;
+
+/* ------------------------------------------------------------------ grid */
+struct Grid {
+  int n[3];
+  int g;
+  int e[3];      /* extents with ghosts */
+  long s[3];     /* strides */
+  long size;
+  explicit Grid(const ob_box* b) {
+    n[0] = b->nx; n[1] = b->ny; n[2] = b->nz; g = b->ng;
+    for (int d = 0; d < 3; d++) e[d] = n[d] + 2 * g;
+    s[0] = 1; s[1] = e[0]; s[2] = (long)e[0] * e[1];
+    size = s[2] * e[2];
+  }
+  long at(int i, int j, int k) const {
+    return (long)(i + g) * s[0] + (long)(j + g) * s[1] + (long)(k + g) * s[2];
+  }
+};
+
+/* slot m of the normal frame for direction d -> component of q or U
+ * m: 0 density, 1 normal velocity, 2 and 3 transverse velocities, 4 pressure/energy */
+static int comp(int d, int m) {
+  if (m == 0 || m == 4) return m;
+  return 1 + (d + (m - 1)) % 3;
+}
+
+static int box_ok(const ob_box* b) {
+  if (b->ng < 4) return 0;
+  if (b->nx < 4 || b->ny < 4 || b->nz < 4) return 0;
+  for (int a = 0; a < 3; a++) {
+    int lo = b->bc[2 * a], hi = b->bc[2 * a + 1];
+    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return 0;
+    if ((lo == OB_PERIODIC) != (hi == OB_PERIODIC)) return 0;
+    if (!(b->dx[a] > 0.0)) return 0;
+  }
+  return b->gamma > 1.0 && b->cfl > 0.0;
+}
+
+/* ------------------------------------------------------- a1: ghost fill (R8) */
+static void fill_ghosts(const ob_box* b, const Grid& G, double* U) {
+  for (int d = 0; d < 3; d++) {
+    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    /* transverse ranges: axes before d are extended (already filled), later ones interior */
+    int lo1 = t1 < d ? -G.g : 0, hi1 = t1 < d ? G.n[t1] + G.g : G.n[t1];
+    int lo2 = t2 < d ? -G.g : 0, hi2 = t2 < d ? G.n[t2] + G.g : G.n[t2];
+    int n = G.n[d];
+    for (int a = lo1; a < hi1; a++) {
+      for (int c = lo2; c < hi2; c++) {
+        for (int side = 0; side < 2; side++) {
+          int bc = b->bc[2 * d + side];
+          for (int m = 1; m <= G.g; m++) {
+            int gi = side == 0 ? -m : n - 1 + m;
+            int si;
+            if (bc == OB_PERIODIC) si = side == 0 ? n - m : m - 1;
+            else if (bc == OB_OUTFLOW) si = side == 0 ? 0 : n - 1;
+            else si = side == 0 ? m - 1 : n - m;
+            int idx_g[3], idx_s[3];
+            idx_g[d] = gi; idx_s[d] = si;
+            idx_g[t1] = a; idx_s[t1] = a;
+            idx_g[t2] = c; idx_s[t2] = c;
+            long zg = G.at(idx_g[0], idx_g[1], idx_g[2]);
+            long zs = G.at(idx_s[0], idx_s[1], idx_s[2]);
+            for (int v = 0; v < 5; v++) {
+              double val = U[v * G.size + zs];
+              if (bc == OB_REFLECT && v == 1 + d) val = -val;
+              U[v * G.size + zg] = val;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------- a2: conserved -> primitive */
+static void cons_to_prim_zone(const double* U, long Z, long N, double gamma, double* q, double* c) {
+  double rho = U[Z];
+  if (rho < SMALL_DENS) rho = SMALL_DENS;
+  double u = U[N + Z] / rho;
+  double v = U[2 * N + Z] / rho;
+  double w = U[3 * N + Z] / rho;
+  double kin = 0.5 * rho * (u * u + v * v + w * w);
+  double p = (gamma - 1.0) * (U[4 * N + Z] - kin);
+  if (p < SMALL_PRES) p = SMALL_PRES;
+  q[Z] = rho; q[N + Z] = u; q[2 * N + Z] = v; q[3 * N + Z] = w; q[4 * N + Z] = p;
+  c[Z] = sqrt(gamma * p / rho);
+}
+
+static void cons_to_prim_all(const ob_box* b, const Grid& G, const double* U, double* q, double* c) {
+#pragma omp parallel for schedule(static)
+  for (long Z = 0; Z < G.size; Z++) cons_to_prim_zone(U, Z, G.size, b->gamma, q, c);
+}
+
+/* --------------------------------------------------------------- a11: dt (R7) */
+static double compute_dt(const ob_box* b, const Grid& G, const double* U) {
+  double dtmin = HUGE_VAL;
+  for (int k = 0; k < G.n[2]; k++)
+    for (int j = 0; j < G.n[1]; j++)
+      for (int i = 0; i < G.n[0]; i++) {
+        long Z = G.at(i, j, k);
+        double rho = U[Z];
+        if (rho < SMALL_DENS) rho = SMALL_DENS;
+        double u[3];
+        for (int d = 0; d < 3; d++) u[d] = U[(1 + d) * G.size + Z] / rho;
+        double kin = 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double p = (b->gamma - 1.0) * (U[4 * G.size + Z] - kin);
+        if (p < SMALL_PRES) p = SMALL_PRES;
+        double cs = sqrt(b->gamma * p / rho);
+        for (int d = 0; d < 3; d++) {
+          double t = b->dx[d] / (fabs(u[d]) + cs);
+          if (t < dtmin) dtmin = t;
+        }
+      }
+  return b->cfl * dtmin;
+}
+
+/* ------------------------------------------------------- a3: flattening (R2) */
+/* CW84 §4: shock indicator ft at zone Z along stride s (p pressure, un normal velocity) */
+static double flat_tilde(const double* p, const double* un, long Z, long s) {
+  double dp1 = p[Z + s] - p[Z - s];
+  double dp2 = p[Z + 2 * s] - p[Z - 2 * s];
+  double pmin = fmin(p[Z + s], p[Z - s]);
+  int shock = fabs(dp1) / pmin > FLAT_EPS && un[Z - s] - un[Z + s] > 0.0;
+  if (!shock) return 0.0;
+  if (dp2 == 0.0) return 0.0;
+  double r = FLAT_OMEGA2 * (dp1 / dp2 - FLAT_OMEGA1);
+  return fmax(0.0, fmin(1.0, r));
+}
+
+static double flat_dir(const double* p, const double* un, long Z, long s) {
+  double dp1 = p[Z + s] - p[Z - s];
+  long sh = dp1 >= 0.0 ? s : -s;
+  return fmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s));
+}
+
+static void flatten_all(const Grid& G, const double* q, double* chi) {
+  const double* p = q + 4 * G.size;
+#pragma omp parallel for schedule(static)
+  for (int k = -1; k <= G.n[2]; k++)
+    for (int j = -1; j <= G.n[1]; j++)
+      for (int i = -1; i <= G.n[0]; i++) {
+        long Z = G.at(i, j, k);
+        double f = 0.0;
+        for (int d = 0; d < 3; d++) f = fmax(f, flat_dir(p, q + (1 + d) * G.size, Z, G.s[d]));
+        chi[Z] = f;
+      }
+}
+
+/* ---------------------------------------------------------- a4: PPM (R3) */
+/* van Leer limited slope at the middle of (am, a0, ap): CW84 eq. 1.8 */
+static double limited_slope(double am, double a0, double ap) {
+  double dl = a0 - am, dr = ap - a0;
+  if (dl * dr > 0.0) {
+    double dc = 0.5 * (ap - am);
+    double m = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
+    return copysign(m, dc);
+  }
+  return 0.0;
+}
+
+/* limited parabola of variable a in zone Z along stride s, flattened by f:
+ * interface values (CW84 eq. 1.6), monotonicity limiter (eq. 1.10), then
+ * a_{L,R} <- f a_i + (1-f) a_{L,R} (CW84 §4). */
+static void ppm_parabola(const double* a, long Z, long s, double f, double* aL, double* aR) {
+  double am2 = a[Z - 2 * s], am1 = a[Z - s], a0 = a[Z], ap1 = a[Z + s], ap2 = a[Z + 2 * s];
+  double dm1 = limited_slope(am2, am1, a0);
+  double d0 = limited_slope(am1, a0, ap1);
+  double dp1 = limited_slope(a0, ap1, ap2);
+  double L = am1 + 0.5 * (a0 - am1) - (d0 - dm1) / 6.0;
+  double R = a0 + 0.5 * (ap1 - a0) - (dp1 - d0) / 6.0;
+  if ((R - a0) * (a0 - L) <= 0.0) {
+    L = a0;
+    R = a0;
+  } else {
+    double dA = R - L;
+    double mid = a0 - 0.5 * (L + R);
+    if (dA * mid > dA * dA / 6.0) {
+      L = 3.0 * a0 - 2.0 * R;
+    } else if (-(dA * dA) / 6.0 > dA * mid) {
+      R = 3.0 * a0 - 2.0 * L;
+    }
+  }
+  *aL = f * a0 + (1.0 - f) * L;
+  *aR = f * a0 + (1.0 - f) * R;
+}
+
+/* -------------------------------------------- a5: characteristic tracing (R4) */
+/* Average of the parabola over the part of the zone swept by a wave of
+ * Courant number sig toward the right edge (Iplus) or the left edge (Iminus). */
+static double i_plus(double aL, double aR, double a0, double sig) {
+  double dA = aR - aL, a6 = 6.0 * (a0 - 0.5 * (aL + aR));
+  return aR - 0.5 * sig * (dA - (1.0 - 2.0 * sig / 3.0) * a6);
+}
+static double i_minus(double aL, double aR, double a0, double sig) {
+  double dA = aR - aL, a6 = 6.0 * (a0 - 0.5 * (aL + aR));
+  return aL + 0.5 * sig * (dA + (1.0 - 2.0 * sig / 3.0) * a6);
+}
+
+/* Trace zone Z along stride s.  qn[m] points at the normal-frame field m
+ * (rho, u_n, u_t1, u_t2, p).  Writes the left-edge state qm[5] (the right
+ * state of the low face) and the right-edge state qp[5] (the left state of
+ * the high face), both in the normal frame. */
+static void trace_zone(const double* const qn[5], const double* c, double f, long Z, long s,
+                       double dtdx, double* qm, double* qp) {
+  double aL[5], aR[5], a0[5];
+  for (int m = 0; m < 5; m++) {
+    a0[m] = qn[m][Z];
+    ppm_parabola(qn[m], Z, s, f, &aL[m], &aR[m]);
+  }
+  double rho = a0[0], u = a0[1], cs = c[Z];
+  double lam[3] = {u - cs, u, u + cs};
+
+  for (int side = 0; side < 2; side++) {
+    /* side 0: right edge (toward +s, waves with lambda > 0); side 1: left edge */
+    double ref[5];
+    int fast = side == 0 ? 2 : 0;
+    int reaches_fast = side == 0 ? lam[2] > 0.0 : lam[0] < 0.0;
+    for (int m = 0; m < 5; m++) {
+      if (reaches_fast) {
+        double sig = fabs(lam[fast]) * dtdx;
+        ref[m] = side == 0 ? i_plus(aL[m], aR[m], a0[m], sig) : i_minus(aL[m], aR[m], a0[m], sig);
+      } else {
+        ref[m] = a0[m];
+      }
+    }
+    double beta[3];
+    double out[5];
+    out[2] = ref[2];
+    out[3] = ref[3];
+    for (int w = 0; w < 3; w++) {
+      int reaches = side == 0 ? lam[w] > 0.0 : lam[w] < 0.0;
+      if (!reaches) { beta[w] = 0.0; continue; }
+      double sig = fabs(lam[w]) * dtdx;
+      double I[5];
+      for (int m = 0; m < 5; m++)
+        I[m] = side == 0 ? i_plus(aL[m], aR[m], a0[m], sig) : i_minus(aL[m], aR[m], a0[m], sig);
+      double dr = ref[0] - I[0], du = ref[1] - I[1], dp = ref[4] - I[4];
+      if (w == 0) beta[w] = -rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
+      else if (w == 2) beta[w] = rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
+      else {
+        beta[w] = dr - dp / (cs * cs);
+        out[2] = I[2];
+        out[3] = I[3];
+      }
+    }
+    out[0] = ref[0] - (beta[0] + beta[1] + beta[2]);
+    out[1] = ref[1] - (cs / rho) * (beta[2] - beta[0]);
+    out[4] = ref[4] - cs * cs * (beta[0] + beta[2]);
+    if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
+    if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+    double* dst = side == 0 ? qp : qm;
+    for (int m = 0; m < 5; m++) dst[m] = out[m];
+  }
+}
+
+/* --------------------------------------------------------- a9: HLLC (R5) */
+/* Normal-frame states L, R = (rho, u_n, u_t1, u_t2, p) -> normal-frame flux F. */
+static void hllc_normal(const double* L, const double* R, double gamma, double* F) {
+  double rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
+  double rr = R[0], ur = R[1], vr = R[2], wr = R[3], pr = R[4];
+  double El = pl / (gamma - 1.0) + 0.5 * rl * (ul * ul + vl * vl + wl * wl);
+  double Er = pr / (gamma - 1.0) + 0.5 * rr * (ur * ur + vr * vr + wr * wr);
+  double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+  double Hl = (El + pl) / rl, Hr = (Er + pr) / rr;
+  double sl = sqrt(rl), sr = sqrt(rr);
+  double ut = (sl * ul + sr * ur) / (sl + sr);
+  double vt = (sl * vl + sr * vr) / (sl + sr);
+  double wt = (sl * wl + sr * wr) / (sl + sr);
+  double Ht = (sl * Hl + sr * Hr) / (sl + sr);
+  double ct2 = (gamma - 1.0) * (Ht - 0.5 * (ut * ut + vt * vt + wt * wt));
+  double SL, SR;
+  if (ct2 > 0.0) {
+    double ct = sqrt(ct2);
+    SL = fmin(ul - cl, ut - ct);
+    SR = fmax(ur + cr, ut + ct);
+  } else {
+    SL = fmin(ul - cl, ur - cr);
+    SR = fmax(ul + cl, ur + cr);
+  }
+  double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur));
+
+  double FL[5] = {rl * ul, rl * ul * ul + pl, rl * ul * vl, rl * ul * wl, (El + pl) * ul};
+  double FR[5] = {rr * ur, rr * ur * ur + pr, rr * ur * vr, rr * ur * wr, (Er + pr) * ur};
+  if (SL >= 0.0) {
+    for (int m = 0; m < 5; m++) F[m] = FL[m];
+  } else if (SR <= 0.0) {
+    for (int m = 0; m < 5; m++) F[m] = FR[m];
+  } else if (Ss >= 0.0) {
+    double Ul[5] = {rl, rl * ul, rl * vl, rl * wl, El};
+    double fac = rl * (SL - ul) / (SL - Ss);
+    double Us[5] = {fac, fac * Ss, fac * vl, fac * wl,
+                    fac * (El / rl + (Ss - ul) * (Ss + pl / (rl * (SL - ul))))};
+    for (int m = 0; m < 5; m++) F[m] = FL[m] + SL * (Us[m] - Ul[m]);
+  } else {
+    double Ur[5] = {rr, rr * ur, rr * vr, rr * wr, Er};
+    double fac = rr * (SR - ur) / (SR - Ss);
+    double Us[5] = {fac, fac * Ss, fac * vr, fac * wr,
+                    fac * (Er / rr + (Ss - ur) * (Ss + pr / (rr * (SR - ur))))};
+    for (int m = 0; m < 5; m++) F[m] = FR[m] + SR * (Us[m] - Ur[m]);
+  }
+}
+
+/* HLLC across a face normal to d, states and flux in x,y,z components. */
+static void hllc_xyz(int d, const double* qL, const double* qR, double gamma, double* F) {
+  double L[5], R[5], Fn[5];
+  for (int m = 0; m < 5; m++) {
+    L[m] = qL[comp(d, m)];
+    R[m] = qR[comp(d, m)];
+  }
+  hllc_normal(L, R, gamma, Fn);
+  for (int m = 0; m < 5; m++) F[comp(d, m)] = Fn[m];
+}
+
+/* ------------------------------------------------ helpers for the CTU stages */
+static void prim_to_cons(const double* q, double gamma, double* U) {
+  U[0] = q[0];
+  U[1] = q[0] * q[1];
+  U[2] = q[0] * q[2];
+  U[3] = q[0] * q[3];
+  U[4] = q[4] / (gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+}
+
+/* returns 0 (and leaves q alone) when the state has rho <= 0 or p <= 0 (R6) */
+static int cons_to_prim_checked(const double* U, double gamma, double* q) {
+  if (!(U[0] > 0.0)) return 0;
+  double u = U[1] / U[0], v = U[2] / U[0], w = U[3] / U[0];
+  double p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w));
+  if (!(p > 0.0)) return 0;
+  q[0] = U[0]; q[1] = u; q[2] = v; q[3] = w;
+  q[4] = p < SMALL_PRES ? SMALL_PRES : p;
+  return 1;
+}
+
+/* ------------------------------------------------------------- workspace */
+/* field order (each G.size doubles): q[5], c, chi, qm[3][5], qp[3][5],
+ * F0[3][5], F1[6][5] (pairs xy,xz,yx,yz,zx,zy), F[3][5] -> 97 fields */
+enum {
+  W_Q = 0, W_C = 5, W_CHI = 6, W_QM = 7, W_QP = 22, W_F0 = 37, W_F1 = 52, W_F = 82, W_NFIELDS = 97
+};
+static int pair_index(int d, int e) {
+  /* (0,1)->0 (0,2)->1 (1,0)->2 (1,2)->3 (2,0)->4 (2,1)->5 */
+  return 2 * d + (e > d ? e - 1 : e);
+}
+
+/* state of a d-face side, stored per zone in the normal frame, back to x,y,z */
+static void load_state(const double* W, long N, int base, int d, long Z, double* q) {
+  for (int m = 0; m < 5; m++) q[comp(d, m)] = W[(long)(base + 5 * d + m) * N + Z];
+}
+
+/* ------------------------------------------------------------- one step */
+static void trace_all(const ob_box* b, const Grid& G, double dt, double* W) {
+  long N = G.size;
+  for (int d = 0; d < 3; d++) {
+    double dtdx = dt / b->dx[d];
+    const double* qn[5];
+    for (int m = 0; m < 5; m++) qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+#pragma omp parallel for schedule(static)
+    for (int k = -1; k <= G.n[2]; k++)
+      for (int j = -1; j <= G.n[1]; j++)
+        for (int i = -1; i <= G.n[0]; i++) {
+          long Z = G.at(i, j, k);
+          double qm[5], qp[5];
+          trace_zone(qn, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, G.s[d], dtdx, qm, qp);
+          for (int m = 0; m < 5; m++) {
+            W[(long)(W_QM + 5 * d + m) * N + Z] = qm[m];
+            W[(long)(W_QP + 5 * d + m) * N + Z] = qp[m];
+          }
+        }
+  }
+}
+
+/* loop bounds for faces normal to d: normal index lo..n_d, transverse per mode */
+static void face_range(const Grid& G, int d, const int* tlo, const int* thi, int* lo, int* hi) {
+  for (int a = 0; a < 3; a++) {
+    if (a == d) { lo[a] = 0; hi[a] = G.n[a]; }
+    else { lo[a] = tlo[a]; hi[a] = thi[a]; }
+  }
+}
+
+static void normal_fluxes(const ob_box* b, const Grid& G, double* W) {
+  long N = G.size;
+  for (int d = 0; d < 3; d++) {
+    int tlo[3] = {-1, -1, -1}, thi[3] = {G.n[0], G.n[1], G.n[2]}, lo[3], hi[3];
+    face_range(G, d, tlo, thi, lo, hi);
+#pragma omp parallel for schedule(static)
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          long Z = G.at(i, j, k);
+          double qL[5], qR[5], F[5];
+          load_state(W, N, W_QP, d, Z - G.s[d], qL);
+          load_state(W, N, W_QM, d, Z, qR);
+          hllc_xyz(d, qL, qR, b->gamma, F);
+          for (int v = 0; v < 5; v++) W[(long)(W_F0 + 5 * d + v) * N + Z] = F[v];
+        }
+  }
+}
+
+/* conserved correction of a face state belonging to zone Z */
+static void corrected_state(const ob_box* b, const double* qin, int nterms, const double* fac,
+                            const double* const* Fs, const long* s, long Z, long N, double* qout) {
+  double U[5];
+  prim_to_cons(qin, b->gamma, U);
+  for (int v = 0; v < 5; v++) {
+    double val = U[v];
+    for (int t = 0; t < nterms; t++) val = val - fac[t] * (Fs[t][v * N + Z + s[t]] - Fs[t][v * N + Z]);
+    U[v] = val;
+  }
+  for (int v = 0; v < 5; v++) qout[v] = qin[v];
+  cons_to_prim_checked(U, b->gamma, qout);
+}
+
+static void ctu_stage1(const ob_box* b, const Grid& G, double dt, double* W) {
+  long N = G.size;
+  for (int d = 0; d < 3; d++)
+    for (int e = 0; e < 3; e++) {
+      if (e == d) continue;
+      int f = 3 - d - e;
+      int tlo[3], thi[3], lo[3], hi[3];
+      tlo[e] = 0; thi[e] = G.n[e] - 1;
+      tlo[f] = -1; thi[f] = G.n[f];
+      face_range(G, d, tlo, thi, lo, hi);
+      double fac = dt / (3.0 * b->dx[e]);
+      const double* Fe = W + (long)(W_F0 + 5 * e) * N;
+      long se = G.s[e];
+      double* out = W + (long)(W_F1 + 5 * pair_index(d, e)) * N;
+#pragma omp parallel for schedule(static)
+      for (int k = lo[2]; k <= hi[2]; k++)
+        for (int j = lo[1]; j <= hi[1]; j++)
+          for (int i = lo[0]; i <= hi[0]; i++) {
+            long Z = G.at(i, j, k);
+            long ZL = Z - G.s[d];
+            double qL0[5], qR0[5], qL[5], qR[5], F[5];
+            load_state(W, N, W_QP, d, ZL, qL0);
+            load_state(W, N, W_QM, d, Z, qR0);
+            corrected_state(b, qL0, 1, &fac, &Fe, &se, ZL, N, qL);
+            corrected_state(b, qR0, 1, &fac, &Fe, &se, Z, N, qR);
+            hllc_xyz(d, qL, qR, b->gamma, F);
+            for (int v = 0; v < 5; v++) out[v * N + Z] = F[v];
+          }
+    }
+}
+
+static void ctu_stage2(const ob_box* b, const Grid& G, double dt, double* W) {
+  long N = G.size;
+  for (int d = 0; d < 3; d++) {
+    int e = (d + 1) % 3, f = (d + 2) % 3;
+    int tlo[3] = {0, 0, 0}, thi[3] = {G.n[0] - 1, G.n[1] - 1, G.n[2] - 1}, lo[3], hi[3];
+    face_range(G, d, tlo, thi, lo, hi);
+    double fac[2] = {dt / (2.0 * b->dx[e]), dt / (2.0 * b->dx[f])};
+    const double* Fs[2] = {W + (long)(W_F1 + 5 * pair_index(e, f)) * N,
+                           W + (long)(W_F1 + 5 * pair_index(f, e)) * N};
+    long s[2] = {G.s[e], G.s[f]};
+    double* out = W + (long)(W_F + 5 * d) * N;
+#pragma omp parallel for schedule(static)
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          long Z = G.at(i, j, k);
+          long ZL = Z - G.s[d];
+          double qL0[5], qR0[5], qL[5], qR[5], F[5];
+          load_state(W, N, W_QP, d, ZL, qL0);
+          load_state(W, N, W_QM, d, Z, qR0);
+          corrected_state(b, qL0, 2, fac, Fs, s, ZL, N, qL);
+          corrected_state(b, qR0, 2, fac, Fs, s, Z, N, qR);
+          hllc_xyz(d, qL, qR, b->gamma, F);
+          for (int v = 0; v < 5; v++) out[v * N + Z] = F[v];
+        }
+  }
+}
+
+/* a10: conservative update of the interior; returns 0 when a zone is nonphysical */
+static int update(const ob_box* b, const Grid& G, double dt, double* U, const double* W) {
+  long N = G.size;
+  double dtdx[3];
+  for (int d = 0; d < 3; d++) dtdx[d] = dt / b->dx[d];
+  int ok = 1;
+#pragma omp parallel for schedule(static) reduction(&& : ok)
+  for (int k = 0; k < G.n[2]; k++)
+    for (int j = 0; j < G.n[1]; j++)
+      for (int i = 0; i < G.n[0]; i++) {
+        long Z = G.at(i, j, k);
+        for (int v = 0; v < 5; v++) {
+          double val = U[v * N + Z];
+          for (int d = 0; d < 3; d++) {
+            const double* F = W + (long)(W_F + 5 * d + v) * N;
+            val = val - dtdx[d] * (F[Z + G.s[d]] - F[Z]);
+          }
+          U[v * N + Z] = val;
+        }
+        double rho = U[Z];
+        double kin = 0.5 * (U[N + Z] * U[N + Z] + U[2 * N + Z] * U[2 * N + Z] + U[3 * N + Z] * U[3 * N + Z]) / rho;
+        double p = (b->gamma - 1.0) * (U[4 * N + Z] - kin);
+        if (!(rho > 0.0) || !(p > 0.0) || p != p) ok = 0;
+      }
+  return ok;
+}
+
+static int step_impl(const ob_box* b, double* U, double dt, double* W) {
+  Grid G(b);
+  cons_to_prim_all(b, G, U, W + (long)W_Q * G.size, W + (long)W_C * G.size);
+  flatten_all(G, W + (long)W_Q * G.size, W + (long)W_CHI * G.size);
+  trace_all(b, G, dt, W);
+  normal_fluxes(b, G, W);
+  ctu_stage1(b, G, dt, W);
+  ctu_stage2(b, G, dt, W);
+  return update(b, G, dt, U, W);
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+  omp_set_num_threads(nthreads > 0 ? nthreads : 1);
+#else
+  (void)nthreads;
+#endif
+}
+
+/* ============================================================ exported API
+ * Return codes: 0 ok, -1 invalid box, -3 nonphysical state after an update. */
+extern "C" {
+
+int oracle_nfields(void) { return W_NFIELDS; }
+
+int oracle_fill_ghosts(const ob_box* b, double* U) {
+  if (!box_ok(b)) return -1;
+  Grid G(b);
+  fill_ghosts(b, G, U);
+  return 0;
+}
+
+int oracle_compute_dt(const ob_box* b, const double* U, double* dt) {
+  if (!box_ok(b)) return -1;
+  Grid G(b);
+  *dt = compute_dt(b, G, U);
+  return 0;
+}
+
+int oracle_prim(const ob_box* b, const double* U, double* q, double* c) {
+  if (!box_ok(b)) return -1;
+  Grid G(b);
+  cons_to_prim_all(b, G, U, q, c);
+  return 0;
+}
+
+/* One update with a given dt; the ghost zones of U must already be filled.
+ * work: NULL, or W_NFIELDS * Ng doubles that receive every intermediate. */
+int oracle_step(const ob_box* b, double* U, double dt, double* work, int nthreads) {
+  if (!box_ok(b)) return -1;
+  set_threads(nthreads);
+  Grid G(b);
+  double* W = work;
+  if (!W) W = (double*)calloc((size_t)W_NFIELDS * G.size, sizeof(double));
+  if (!W) return -2;
+  int ok = step_impl(b, U, dt, W);
+  if (!work) free(W);
+  return ok ? 0 : -3;
+}
+
+/* nsteps of: fill ghosts, dt from the state, update.  dts[s] receives each dt
+ * (may be NULL); *t receives the sum. */
+int oracle_run(const ob_box* b, double* U, int nsteps, double* dts, double* t, int nthreads) {
+  if (!box_ok(b) || nsteps < 0) return -1;
+  set_threads(nthreads);
+  Grid G(b);
+  double* W = (double*)calloc((size_t)W_NFIELDS * G.size, sizeof(double));
+  if (!W) return -2;
+  double time = 0.0;
+  int rc = 0;
+  for (int s = 0; s < nsteps; s++) {
+    fill_ghosts(b, G, U);
+    double dt = compute_dt(b, G, U);
+    if (dts) dts[s] = dt;
+    if (!step_impl(b, U, dt, W)) { rc = -3; time += dt; break; }
+    time += dt;
+  }
+  fill_ghosts(b, G, U);
+  free(W);
+  if (t) *t = time;
+  return rc;
+}
+
+/* Stage-level entry points for unit tests --------------------------------- */
+
+/* HLLC flux across a face normal to d for x,y,z primitive states */
+void oracle_hllc(int d, const double* qL, const double* qR, double gamma, double* F) {
+  hllc_xyz(d, qL, qR, gamma, F);
+}
+
+/* PPM parabola of a 1D line a[n] with flattening chi[n]; zones 2..n-3 are written */
+void oracle_ppm_line(const double* a, const double* chi, int n, double* aL, double* aR) {
+  for (long i = 2; i < n - 2; i++) ppm_parabola(a, i, 1, chi[i], &aL[i], &aR[i]);
+}
+
+/* limited slope of (am, a0, ap) */
+double oracle_limited_slope(double am, double a0, double ap) { return limited_slope(am, a0, ap); }
+
+/* tracing of a 1D line: q[5][n] normal-frame primitive, c[n], chi[n];
+ * zones 2..n-3 get qm[5][n], qp[5][n] */
+void oracle_trace_line(const double* q, const double* c, const double* chi, int n, double dtdx,
+                       double* qm, double* qp) {
+  const double* qn[5];
+  for (int m = 0; m < 5; m++) qn[m] = q + (long)m * n;
+  for (long i = 2; i < n - 2; i++) {
+    double a[5], bq[5];
+    trace_zone(qn, c, chi[i], i, 1, dtdx, a, bq);
+    for (int m = 0; m < 5; m++) {
+      qm[(long)m * n + i] = a[m];
+      qp[(long)m * n + i] = bq[m];
+    }
+  }
+}
+
+/* flattening coefficient of a 1D line along x: p[n], u[n]; zones 3..n-4 written */
+void oracle_flatten_line(const double* p, const double* u, int n, double* f) {
+  for (long i = 3; i < n - 3; i++) f[i] = flat_dir(p, u, i, 1);
+}
+
+}  /* extern "C" */
