@@ -1,0 +1,182 @@
+/*
+ * hydro.h -- C ABI of the GB300 hydro library (libhydro_gb300.so).
+ *
+ * The library advances boxes of the 3D compressible Euler equations for an
+ * ideal gamma-law gas by unsplit PPM Godunov steps: conserved-to-primitive
+ * conversion, PPM reconstruction with monotonicity limiters and shock
+ * flattening, characteristic tracing to half-step face states, 3D
+ * corner-transport-upwind (CTU) transverse corrections, HLLC Riemann solves,
+ * the conservative flux-divergence update and the CFL time-step reduction.
+ *
+ * Source of the operations.  The paper (Katz et al., "Preparing Nuclear
+ * Astrophysics for Exascale") states the problem: data lives in boxes
+ * ("Fabs") bounded by lo/hi indices with several components (§2, Fig. 1),
+ * is kept resident on the GPU for the whole run (§3, memory management),
+ * and is advanced by a stencil that computes limited slopes from
+ * neighbouring zones and reconstructs a polynomial of the fluid state (§3);
+ * throughput is reported as zones updated per unit time (§4).  The numerical
+ * method itself is the published PPM/CTU/HLLC family the paper's code uses
+ * (Colella & Woodward 1984; Colella 1990; Saltzman 1994; Toro, Spruce &
+ * Speares 1994).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_dev are CUDA device pointers on the current device;
+ *    pointers named *_host are host pointers (pinned memory gives the best
+ *    copy speed but is not required).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Every call returns an int status: HYDRO_OK (0), HYDRO_PENDING (> 0, poll
+ *    only) or a negative HYDRO_ERR_* code.  hydro_last_error() returns a
+ *    thread-local message describing the last failure.  No exception crosses
+ *    the ABI.
+ *  - Launching calls are asynchronous: device-side errors (a nonphysical state
+ *    after an update) are reported by the next hydro_sync().
+ *  - The library never allocates device memory: the caller passes the state
+ *    and scratch buffers (sized by hydro_workspace_size) and keeps ownership.
+ */
+#ifndef HYDRO_GB300_H
+#define HYDRO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HYDRO_OK 0
+#define HYDRO_PENDING 1
+#define HYDRO_ERR_INVALID (-1)     /* bad argument or descriptor */
+#define HYDRO_ERR_NOMEM (-2)       /* buffer too small or over the memory budget */
+#define HYDRO_ERR_NONPHYSICAL (-3) /* rho <= 0, p <= 0 or NaN after an update */
+#define HYDRO_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define HYDRO_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+
+/* ---- boundary conditions (one per box face) ---- */
+#define HYDRO_BC_PERIODIC 0 /* copy from the opposite side; must be set on both faces of an axis */
+#define HYDRO_BC_OUTFLOW 1  /* zero-gradient copy of the last interior zone */
+#define HYDRO_BC_REFLECT 2  /* mirror image, normal momentum negated */
+
+/* ---- precision of the reconstruction/Riemann stages ---- */
+#define HYDRO_FP64 0  /* every stage in FP64 */
+#define HYDRO_MIXED 1 /* reserved: FP32 reconstruction/tracing/Riemann, FP64 update and dt */
+
+#define HYDRO_NG 4 /* ghost zones per side (the only supported value) */
+
+/* One box.  Zones are (i,j,k) with i in [0,nx) interior and [-ng, nx+ng) with ghosts. */
+typedef struct hydro_box_desc {
+  int32_t nx, ny, nz; /* interior zones per axis, each >= 4 */
+  int32_t ng;         /* ghost zones per side: HYDRO_NG */
+  double dx, dy, dz;  /* zone widths, > 0 */
+  double gamma;       /* ratio of specific heats, > 1 */
+  double cfl;         /* Courant number, in (0, 1] */
+  int32_t bc[6];      /* HYDRO_BC_* for faces xlo, xhi, ylo, yhi, zlo, zhi */
+  int32_t precision;  /* HYDRO_FP64 */
+} hydro_box_desc;
+
+/* Where box `box` lives inside the state buffer, in FP64 elements.
+ * Conserved variable v (0 rho, 1 rho*u, 2 rho*v, 3 rho*w, 4 E) of zone (i,j,k),
+ * ghosts included, is element
+ *   offset + v*var_stride + (k+ng)*plane + (j+ng)*pitch + (i+ng).        */
+typedef struct hydro_layout {
+  int64_t offset;     /* first element of the box */
+  int64_t pitch;      /* elements between rows: nx+2ng rounded up to a multiple of 4 */
+  int64_t plane;      /* elements between planes: pitch*(ny+2ng) */
+  int64_t var_stride; /* elements between variables: plane*(nz+2ng) rounded up to 32 */
+} hydro_layout;
+
+typedef struct hydro_handle hydro_handle;
+
+/* Bytes of device memory needed for `nboxes` boxes described by d[0..nboxes-1]:
+ * the FP64 state (all boxes, ghosts included) and the scratch space (face
+ * states, fluxes, per-box time-step data).  Returns HYDRO_ERR_INVALID for a bad
+ * descriptor (the message names the box and field). */
+int hydro_workspace_size(const hydro_box_desc* d, int nboxes, size_t* state_bytes,
+                         size_t* scratch_bytes);
+
+/* Layout of box `box` in the state buffer (see hydro_layout). */
+int hydro_box_layout(const hydro_box_desc* d, int nboxes, int box, hydro_layout* out);
+
+/* Creates a handle over caller-owned device buffers of at least the sizes
+ * given by hydro_workspace_size.  state_dev and scratch_dev must be 256-byte
+ * aligned and stay valid until hydro_free.  Copies the box table into the
+ * head of scratch_dev (synchronously) and zeroes the per-box time, dt and
+ * status.  The state contents are left alone.  *out receives the handle. */
+int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t state_bytes,
+                void* scratch_dev, size_t scratch_bytes, hydro_handle** out);
+
+/* Releases the handle (host memory only; the caller frees the buffers). */
+int hydro_free(hydro_handle* h);
+
+/* Fills the ghost zones of every box from its boundary conditions, in the
+ * order x, then y, then z, so that edges and corners are filled too. */
+int hydro_fill_ghosts(hydro_handle* h, void* stream);
+
+/* Computes each box's CFL time step from its current interior state,
+ * dt_b = cfl * min over zones and axes of dx_a / (|u_a| + c), into
+ * dt_dev[0..nboxes-1] (device memory, written asynchronously). */
+int hydro_compute_dt(hydro_handle* h, double* dt_dev, void* stream);
+
+/* Advances every box by `nsteps` steps.  Each step fills the ghost zones,
+ * takes dt from dt_dev[b] (or, if dt_dev is NULL, computes it from the state
+ * as hydro_compute_dt does) and applies one unsplit PPM/CTU/HLLC update to the
+ * interior.  nsteps == 0 does nothing.  Asynchronous on `stream`. */
+int hydro_step(hydro_handle* h, const double* dt_dev, int nsteps, void* stream);
+
+/* Waits for `stream`, then reports the first device-side error of any box:
+ * HYDRO_ERR_NONPHYSICAL if an update produced rho <= 0, p <= 0 or NaN.  The
+ * error flags are cleared after being reported. */
+int hydro_sync(hydro_handle* h, void* stream);
+
+/* Simulated time advanced so far by each box, into time_host[0..nboxes-1]
+ * (synchronous on `stream`). */
+int hydro_get_time(hydro_handle* h, double* time_host, void* stream);
+
+/* Copies interior states between host memory and the device state.
+ * The host array is [box][v][k][j][i] over interior zones only, boxes in
+ * order, FP64, exactly sum_b 5*nx*ny*nz*8 bytes (`bytes` must match).  The
+ * copy goes through the scratch space (which it overwrites) and a gather/
+ * scatter kernel; both calls return once the host buffer may be reused. */
+int hydro_upload(hydro_handle* h, const double* state_host, size_t bytes, void* stream);
+int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stream);
+
+/* Diagnostics: where the per-zone intermediates of box `box` live inside the
+ * scratch buffer, for stage-by-stage checks.  *offset receives the element
+ * (FP64) offset of the box's first field from the start of scratch_dev and
+ * *nfields the number of fields (97).  Each field is a ghosted-box grid with
+ * the state's pitch, plane and var_stride (fields are var_stride apart), in
+ * this order: primitive q[5] = (rho,u,v,w,p); sound speed c; flattening
+ * coefficient chi; left-edge states qm[3][5] and right-edge states qp[3][5]
+ * per axis d in the normal frame of d (rho, u_d, u_{d+1}, u_{d+2}, p, axis
+ * indices mod 3); normal fluxes f0[3][5]; once-corrected fluxes f1[6][5] for
+ * the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes f[3][5].  Fluxes are
+ * conserved-variable components; the flux through the low face of zone
+ * (i,j,k) along d is stored at (i,j,k).  Values are defined only where the
+ * step computes them (see the regions in the library documentation). */
+int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset, int32_t* nfields);
+
+/* Number of kernels this handle has launched since hydro_alloc (a ghost fill
+ * is three kernels, every other stage one), into *count. */
+int hydro_kernel_launches(hydro_handle* h, int64_t* count);
+
+/* Per-stage device time.  Between hydro_profile_begin and hydro_profile_end
+ * every stage launch is bracketed by a pair of CUDA events recorded on the
+ * launching stream.  hydro_profile_end waits for those events and writes one
+ * record per stage (up to max_stages, in launch order; *nstages receives the
+ * number of stages): kernels launched and summed device milliseconds. */
+typedef struct hydro_stage_time {
+  char name[24];    /* fill_ghosts, prim, dt, flatten, trace, riemann, ctu1, ctu2, update */
+  int64_t launches; /* kernels launched in the stage while profiling */
+  double total_ms;  /* summed event time of those launches */
+} hydro_stage_time;
+int hydro_profile_begin(hydro_handle* h);
+int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, int* nstages);
+
+/* Thread-local description of the last error (never NULL). */
+const char* hydro_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_GB300_H */

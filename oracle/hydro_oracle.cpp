@@ -23,6 +23,9 @@
  *       one coefficient per zone = max over the three directions.
  *   R3  PPM (CW84 eqs. 1.6-1.10): van Leer limited slopes, 4th-order
  *       interface values, CW84 monotonicity limiter, then flattening blend.
+ *       Slopes are stored per zone and interface values per face, so every
+ *       quantity of the method is computed once (the operation counts of
+ *       flop_count.cpp are then the method's algorithmic work).
  *   R4  tracing: reference state = integral of the parabola under the fastest
  *       wave moving toward the edge (zone value if none), characteristic
  *       projection with zone-centred rho and c; waves with lambda == 0 excluded.
@@ -228,16 +231,16 @@ static double limited_slope(double am, double a0, double ap) {
   return 0.0;
 }
 
-/* limited parabola of variable a in zone Z along stride s, flattened by f:
- * interface values (CW84 eq. 1.6), monotonicity limiter (eq. 1.10), then
- * a_{L,R} <- f a_i + (1-f) a_{L,R} (CW84 §4). */
-static void ppm_parabola(const double* a, long Z, long s, double f, double* aL, double* aR) {
-  double am2 = a[Z - 2 * s], am1 = a[Z - s], a0 = a[Z], ap1 = a[Z + s], ap2 = a[Z + 2 * s];
-  double dm1 = limited_slope(am2, am1, a0);
-  double d0 = limited_slope(am1, a0, ap1);
-  double dp1 = limited_slope(a0, ap1, ap2);
-  double L = am1 + 0.5 * (a0 - am1) - (d0 - dm1) / 6.0;
-  double R = a0 + 0.5 * (ap1 - a0) - (dp1 - d0) / 6.0;
+/* 4th-order value at the interface between zones Z-s and Z (CW84 eq. 1.6),
+ * from zone values a and limited slopes dm */
+static double interface_value(const double* a, const double* dm, long Z, long s) {
+  return a[Z - s] + 0.5 * (a[Z] - a[Z - s]) - (dm[Z] - dm[Z - s]) / 6.0;
+}
+
+/* Parabola of zone value a0 between interface values (L, R): CW84 monotonicity
+ * limiter (eq. 1.10), then a_{L,R} <- f a0 + (1-f) a_{L,R} (CW84 §4). */
+static void limit_parabola(double a0, double f, double* aL, double* aR) {
+  double L = *aL, R = *aR;
   if ((R - a0) * (a0 - L) <= 0.0) {
     L = a0;
     R = a0;
@@ -267,21 +270,26 @@ static double i_minus(double aL, double aR, double a0, double sig) {
 }
 
 /* Trace zone Z along stride s.  qn[m] points at the normal-frame field m
- * (rho, u_n, u_t1, u_t2, p).  Writes the left-edge state qm[5] (the right
- * state of the low face) and the right-edge state qp[5] (the left state of
- * the high face), both in the normal frame. */
-static void trace_zone(const double* const qn[5], const double* c, double f, long Z, long s,
-                       double dtdx, double* qm, double* qp) {
+ * (rho, u_n, u_t1, u_t2, p) and face[m] at its interface values (value at the
+ * low face of each zone).  Writes the left-edge state qm[5] (the right state
+ * of the low face) and the right-edge state qp[5] (the left state of the high
+ * face), both in the normal frame. */
+static void trace_zone(const double* const qn[5], const double* const face[5], const double* c, double f,
+                       long Z, long s, double dtdx, double* qm, double* qp) {
   double aL[5], aR[5], a0[5];
   for (int m = 0; m < 5; m++) {
     a0[m] = qn[m][Z];
-    ppm_parabola(qn[m], Z, s, f, &aL[m], &aR[m]);
+    aL[m] = face[m][Z];
+    aR[m] = face[m][Z + s];
+    limit_parabola(a0[m], f, &aL[m], &aR[m]);
   }
   double rho = a0[0], u = a0[1], cs = c[Z];
   double lam[3] = {u - cs, u, u + cs};
 
   for (int side = 0; side < 2; side++) {
-    /* side 0: right edge (toward +s, waves with lambda > 0); side 1: left edge */
+    /* side 0: right edge (toward +s, waves with lambda > 0); side 1: left edge.
+     * The fastest wave toward the edge supplies the reference state; its own
+     * amplitude is zero by construction and is not formed. */
     double ref[5];
     int fast = side == 0 ? 2 : 0;
     int reaches_fast = side == 0 ? lam[2] > 0.0 : lam[0] < 0.0;
@@ -293,21 +301,32 @@ static void trace_zone(const double* const qn[5], const double* c, double f, lon
         ref[m] = a0[m];
       }
     }
-    double beta[3];
+    double beta[3] = {0.0, 0.0, 0.0};
     double out[5];
     out[2] = ref[2];
     out[3] = ref[3];
     for (int w = 0; w < 3; w++) {
+      if (w == fast) continue;
       int reaches = side == 0 ? lam[w] > 0.0 : lam[w] < 0.0;
-      if (!reaches) { beta[w] = 0.0; continue; }
+      if (!reaches) continue;
       double sig = fabs(lam[w]) * dtdx;
+      /* integrals of the variables this wave's amplitude uses */
+      const int acoustic[2] = {1, 4}, entropy[4] = {0, 4, 2, 3};
+      const int* vars = w == 1 ? entropy : acoustic;
+      int nv = w == 1 ? 4 : 2;
       double I[5];
-      for (int m = 0; m < 5; m++)
+      for (int k = 0; k < nv; k++) {
+        int m = vars[k];
         I[m] = side == 0 ? i_plus(aL[m], aR[m], a0[m], sig) : i_minus(aL[m], aR[m], a0[m], sig);
-      double dr = ref[0] - I[0], du = ref[1] - I[1], dp = ref[4] - I[4];
-      if (w == 0) beta[w] = -rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
-      else if (w == 2) beta[w] = rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
-      else {
+      }
+      if (w == 0) {
+        double du = ref[1] - I[1], dp = ref[4] - I[4];
+        beta[w] = -rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
+      } else if (w == 2) {
+        double du = ref[1] - I[1], dp = ref[4] - I[4];
+        beta[w] = rho / (2.0 * cs) * du + dp / (2.0 * cs * cs);
+      } else {
+        double dr = ref[0] - I[0], dp = ref[4] - I[4];
         beta[w] = dr - dp / (cs * cs);
         out[2] = I[2];
         out[3] = I[3];
@@ -349,25 +368,29 @@ static void hllc_normal(const double* L, const double* R, double gamma, double* 
   }
   double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur));
 
-  double FL[5] = {rl * ul, rl * ul * ul + pl, rl * ul * vl, rl * ul * wl, (El + pl) * ul};
-  double FR[5] = {rr * ur, rr * ur * ur + pr, rr * ur * vr, rr * ur * wr, (Er + pr) * ur};
-  if (SL >= 0.0) {
-    for (int m = 0; m < 5; m++) F[m] = FL[m];
-  } else if (SR <= 0.0) {
-    for (int m = 0; m < 5; m++) F[m] = FR[m];
-  } else if (Ss >= 0.0) {
+  if (SL >= 0.0 || (SR > 0.0 && Ss >= 0.0)) {
+    double FL[5] = {rl * ul, rl * ul * ul + pl, rl * ul * vl, rl * ul * wl, (El + pl) * ul};
+    if (SL >= 0.0) {
+      for (int m = 0; m < 5; m++) F[m] = FL[m];
+      return;
+    }
     double Ul[5] = {rl, rl * ul, rl * vl, rl * wl, El};
     double fac = rl * (SL - ul) / (SL - Ss);
     double Us[5] = {fac, fac * Ss, fac * vl, fac * wl,
                     fac * (El / rl + (Ss - ul) * (Ss + pl / (rl * (SL - ul))))};
     for (int m = 0; m < 5; m++) F[m] = FL[m] + SL * (Us[m] - Ul[m]);
-  } else {
-    double Ur[5] = {rr, rr * ur, rr * vr, rr * wr, Er};
-    double fac = rr * (SR - ur) / (SR - Ss);
-    double Us[5] = {fac, fac * Ss, fac * vr, fac * wr,
-                    fac * (Er / rr + (Ss - ur) * (Ss + pr / (rr * (SR - ur))))};
-    for (int m = 0; m < 5; m++) F[m] = FR[m] + SR * (Us[m] - Ur[m]);
+    return;
   }
+  double FR[5] = {rr * ur, rr * ur * ur + pr, rr * ur * vr, rr * ur * wr, (Er + pr) * ur};
+  if (SR <= 0.0) {
+    for (int m = 0; m < 5; m++) F[m] = FR[m];
+    return;
+  }
+  double Ur[5] = {rr, rr * ur, rr * vr, rr * wr, Er};
+  double fac = rr * (SR - ur) / (SR - Ss);
+  double Us[5] = {fac, fac * Ss, fac * vr, fac * wr,
+                  fac * (Er / rr + (Ss - ur) * (Ss + pr / (rr * (SR - ur))))};
+  for (int m = 0; m < 5; m++) F[m] = FR[m] + SR * (Us[m] - Ur[m]);
 }
 
 /* HLLC across a face normal to d, states and flux in x,y,z components. */
@@ -418,25 +441,57 @@ static void load_state(const double* W, long N, int base, int d, long Z, double*
 }
 
 /* ------------------------------------------------------------- one step */
+/* a4 + a5 for every direction: limited slopes of the five normal-frame
+ * variables on zones [-2, n_d+1] along d, interface values on the faces
+ * [-1, n_d+1] (each computed once and stored, the CPU structure the paper's
+ * §3 describes), then per zone of [-1, n]^3 the limited parabolas and the
+ * traced edge states. */
 static void trace_all(const ob_box* b, const Grid& G, double dt, double* W) {
   long N = G.size;
+  double* slope = (double*)calloc((size_t)5 * N, sizeof(double));
+  double* face = (double*)calloc((size_t)5 * N, sizeof(double));
   for (int d = 0; d < 3; d++) {
     double dtdx = dt / b->dx[d];
+    long s = G.s[d];
     const double* qn[5];
-    for (int m = 0; m < 5; m++) qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+    const double* fc[5];
+    for (int m = 0; m < 5; m++) {
+      qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+      fc[m] = face + (long)m * N;
+    }
+    int lo[3] = {-1, -1, -1}, hi[3] = {G.n[0], G.n[1], G.n[2]};
+    lo[d] = -2;
+    hi[d] = G.n[d] + 1;
+#pragma omp parallel for schedule(static)
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          long Z = G.at(i, j, k);
+          for (int m = 0; m < 5; m++) slope[(long)m * N + Z] = limited_slope(qn[m][Z - s], qn[m][Z], qn[m][Z + s]);
+        }
+    lo[d] = -1;
+#pragma omp parallel for schedule(static)
+    for (int k = lo[2]; k <= hi[2]; k++)
+      for (int j = lo[1]; j <= hi[1]; j++)
+        for (int i = lo[0]; i <= hi[0]; i++) {
+          long Z = G.at(i, j, k);
+          for (int m = 0; m < 5; m++) face[(long)m * N + Z] = interface_value(qn[m], slope + (long)m * N, Z, s);
+        }
 #pragma omp parallel for schedule(static)
     for (int k = -1; k <= G.n[2]; k++)
       for (int j = -1; j <= G.n[1]; j++)
         for (int i = -1; i <= G.n[0]; i++) {
           long Z = G.at(i, j, k);
           double qm[5], qp[5];
-          trace_zone(qn, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, G.s[d], dtdx, qm, qp);
+          trace_zone(qn, fc, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, s, dtdx, qm, qp);
           for (int m = 0; m < 5; m++) {
             W[(long)(W_QM + 5 * d + m) * N + Z] = qm[m];
             W[(long)(W_QP + 5 * d + m) * N + Z] = qp[m];
           }
         }
   }
+  free(slope);
+  free(face);
 }
 
 /* loop bounds for faces normal to d: normal index lo..n_d, transverse per mode */
@@ -658,7 +713,14 @@ void oracle_hllc(int d, const double* qL, const double* qR, double gamma, double
 
 /* PPM parabola of a 1D line a[n] with flattening chi[n]; zones 2..n-3 are written */
 void oracle_ppm_line(const double* a, const double* chi, int n, double* aL, double* aR) {
-  for (long i = 2; i < n - 2; i++) ppm_parabola(a, i, 1, chi[i], &aL[i], &aR[i]);
+  double* dm = (double*)calloc((size_t)n, sizeof(double));
+  for (long i = 1; i < n - 1; i++) dm[i] = limited_slope(a[i - 1], a[i], a[i + 1]);
+  for (long i = 2; i < n - 2; i++) {
+    aL[i] = interface_value(a, dm, i, 1);
+    aR[i] = interface_value(a, dm, i + 1, 1);
+    limit_parabola(a[i], chi[i], &aL[i], &aR[i]);
+  }
+  free(dm);
 }
 
 /* limited slope of (am, a0, ap) */
@@ -669,15 +731,25 @@ double oracle_limited_slope(double am, double a0, double ap) { return limited_sl
 void oracle_trace_line(const double* q, const double* c, const double* chi, int n, double dtdx,
                        double* qm, double* qp) {
   const double* qn[5];
-  for (int m = 0; m < 5; m++) qn[m] = q + (long)m * n;
+  const double* fc[5];
+  double* dm = (double*)calloc((size_t)n, sizeof(double));
+  double* face = (double*)calloc((size_t)5 * n, sizeof(double));
+  for (int m = 0; m < 5; m++) {
+    qn[m] = q + (long)m * n;
+    fc[m] = face + (long)m * n;
+    for (long i = 1; i < n - 1; i++) dm[i] = limited_slope(qn[m][i - 1], qn[m][i], qn[m][i + 1]);
+    for (long i = 2; i < n - 1; i++) face[(long)m * n + i] = interface_value(qn[m], dm, i, 1);
+  }
   for (long i = 2; i < n - 2; i++) {
     double a[5], bq[5];
-    trace_zone(qn, c, chi[i], i, 1, dtdx, a, bq);
+    trace_zone(qn, fc, c, chi[i], i, 1, dtdx, a, bq);
     for (int m = 0; m < 5; m++) {
       qm[(long)m * n + i] = a[m];
       qp[(long)m * n + i] = bq[m];
     }
   }
+  free(dm);
+  free(face);
 }
 
 /* flattening coefficient of a 1D line along x: p[n], u[n]; zones 3..n-4 written */

@@ -1,0 +1,408 @@
+// C ABI of the hydro library (declared in include/hydro.h): descriptor
+// validation, the memory plan over caller-owned buffers, and the launch
+// sequence of one step.  The library allocates no device memory.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hydro_internal.cuh"
+
+using hydro::BoxRt;
+using hydro::DevBox;
+using hydro::HostBox;
+using hydro::Plan;
+
+struct hydro_handle {
+  Plan plan;
+  std::vector<HostBox> boxes;
+  int device;
+  size_t state_bytes, scratch_bytes;
+  long long launches = 0;            // kernels launched through this handle
+  bool profiling = false;            // record an event pair around every stage launch
+  std::vector<cudaEvent_t> events;   // event pool (pairs), reused across sessions
+  std::vector<int> rec_stage;        // stage of each recorded pair
+};
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(HYDRO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int validate(const hydro_box_desc& d, int i) {
+  char buf[160];
+  auto bad = [&](const char* what) {
+    snprintf(buf, sizeof buf, "box %d: %s", i, what);
+    return fail(HYDRO_ERR_INVALID, buf);
+  };
+  if (d.ng != HYDRO_NG) return bad("ng must be 4");
+  if (d.nx < 4 || d.ny < 4 || d.nz < 4) return bad("every axis needs at least 4 interior zones");
+  if ((long long)(d.nx + 2 * HYDRO_NG) * (d.ny + 2 * HYDRO_NG) * (d.nz + 2 * HYDRO_NG) > (1LL << 31))
+    return bad("box too large (more than 2^31 zones with ghosts)");
+  if (!(d.dx > 0.0) || !(d.dy > 0.0) || !(d.dz > 0.0)) return bad("zone widths must be > 0");
+  if (!(d.gamma > 1.0)) return bad("gamma must be > 1");
+  if (!(d.cfl > 0.0) || d.cfl > 1.0) return bad("cfl must be in (0, 1]");
+  for (int a = 0; a < 3; a++) {
+    const int lo = d.bc[2 * a], hi = d.bc[2 * a + 1];
+    if (lo < HYDRO_BC_PERIODIC || lo > HYDRO_BC_REFLECT || hi < HYDRO_BC_PERIODIC || hi > HYDRO_BC_REFLECT)
+      return bad("unknown boundary condition");
+    if ((lo == HYDRO_BC_PERIODIC) != (hi == HYDRO_BC_PERIODIC)) return bad("periodic faces must pair");
+  }
+  if (d.precision != HYDRO_FP64) return bad("precision must be HYDRO_FP64");
+  return HYDRO_OK;
+}
+
+struct Geometry {
+  std::vector<HostBox> boxes;
+  size_t state_elems = 0;
+  size_t table_bytes = 0, rt_bytes = 0, head_bytes = 0;
+  size_t work_elems = 0, stage_elems = 0;
+  size_t scratch_bytes = 0;
+};
+
+int plan_geometry(const hydro_box_desc* d, int nboxes, Geometry* g) {
+  if (!d || nboxes <= 0) return fail(HYDRO_ERR_INVALID, "need at least one box descriptor");
+  if (nboxes > 65535) return fail(HYDRO_ERR_INVALID, "at most 65535 boxes per handle");
+  g->boxes.resize(nboxes);
+  long long soff = 0, woff = 0, stoff = 0;
+  for (int i = 0; i < nboxes; i++) {
+    int rc = validate(d[i], i);
+    if (rc) return rc;
+    HostBox& hb = g->boxes[i];
+    hb.d = d[i];
+    hb.pitch = (long long)align_up((size_t)(d[i].nx + 2 * HYDRO_NG), 4);
+    hb.plane = hb.pitch * (d[i].ny + 2 * HYDRO_NG);
+    hb.vs = (long long)align_up((size_t)(hb.plane * (d[i].nz + 2 * HYDRO_NG)), 32);
+    hb.interior = (long long)d[i].nx * d[i].ny * d[i].nz;
+    hb.state_off = soff;
+    hb.work_off = woff;
+    hb.stage_off = stoff;
+    soff += 5 * hb.vs;
+    woff += (long long)hydro::NFIELDS * hb.vs;
+    stoff += 5 * hb.interior;
+  }
+  g->state_elems = (size_t)soff;
+  g->work_elems = (size_t)woff;
+  g->stage_elems = (size_t)stoff;
+  g->table_bytes = align_up(sizeof(DevBox) * nboxes, ALIGN);
+  g->rt_bytes = align_up(sizeof(BoxRt) * nboxes, ALIGN);
+  g->head_bytes = g->table_bytes + g->rt_bytes;
+  g->scratch_bytes = g->head_bytes + g->work_elems * sizeof(double);
+  return HYDRO_OK;
+}
+
+int check_device(const hydro_handle* h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != h->device) return fail(HYDRO_ERR_INVALID, "handle used with a different current device");
+  return HYDRO_OK;
+}
+
+int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? HYDRO_OK : cuda_fail(e, what); }
+
+// Launches one stage, bracketed by timing events when profiling is on.
+cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const double* dt_in = nullptr,
+                      double* dt_out = nullptr, int advance = 0) {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (h->profiling) {
+    const size_t need = 2 * (h->rec_stage.size() + 1);
+    while (h->events.size() < need) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      h->events.push_back(e);
+    }
+    ev[0] = h->events[need - 2];
+    ev[1] = h->events[need - 1];
+    cudaError_t err = cudaEventRecord(ev[0], s);
+    if (err != cudaSuccess) return err;
+  }
+  cudaError_t e = hydro::launch_stage(h->plan, st, s, dt_in, dt_out, advance);
+  if (e != cudaSuccess) return e;
+  h->launches += hydro::STAGE_KERNELS[st];
+  if (h->profiling) {
+    e = cudaEventRecord(ev[1], s);
+    h->rec_stage.push_back((int)st);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hydro_last_error(void) { return g_err.c_str(); }
+
+int hydro_workspace_size(const hydro_box_desc* d, int nboxes, size_t* state_bytes, size_t* scratch_bytes) {
+  if (!state_bytes || !scratch_bytes) return fail(HYDRO_ERR_INVALID, "null output pointer");
+  Geometry g;
+  int rc = plan_geometry(d, nboxes, &g);
+  if (rc) return rc;
+  *state_bytes = g.state_elems * sizeof(double);
+  *scratch_bytes = g.scratch_bytes;
+  return HYDRO_OK;
+}
+
+int hydro_box_layout(const hydro_box_desc* d, int nboxes, int box, hydro_layout* out) {
+  if (!out) return fail(HYDRO_ERR_INVALID, "null output pointer");
+  Geometry g;
+  int rc = plan_geometry(d, nboxes, &g);
+  if (rc) return rc;
+  if (box < 0 || box >= nboxes) return fail(HYDRO_ERR_INVALID, "box index out of range");
+  const HostBox& hb = g.boxes[box];
+  out->offset = hb.state_off;
+  out->pitch = hb.pitch;
+  out->plane = hb.plane;
+  out->var_stride = hb.vs;
+  return HYDRO_OK;
+}
+
+int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset, int32_t* nfields) {
+  if (!offset || !nfields) return fail(HYDRO_ERR_INVALID, "null output pointer");
+  Geometry g;
+  int rc = plan_geometry(d, nboxes, &g);
+  if (rc) return rc;
+  if (box < 0 || box >= nboxes) return fail(HYDRO_ERR_INVALID, "box index out of range");
+  *offset = (int64_t)(g.head_bytes / sizeof(double)) + g.boxes[box].work_off;
+  *nfields = hydro::NFIELDS;
+  return HYDRO_OK;
+}
+
+int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t state_bytes, void* scratch_dev,
+                size_t scratch_bytes, hydro_handle** out) {
+  if (!out) return fail(HYDRO_ERR_INVALID, "null output pointer");
+  *out = nullptr;
+  Geometry g;
+  int rc = plan_geometry(d, nboxes, &g);
+  if (rc) return rc;
+  if (!state_dev || !scratch_dev) return fail(HYDRO_ERR_INVALID, "null device buffer");
+  if ((reinterpret_cast<uintptr_t>(state_dev) | reinterpret_cast<uintptr_t>(scratch_dev)) % ALIGN)
+    return fail(HYDRO_ERR_INVALID, "device buffers must be 256-byte aligned");
+  if (state_bytes < g.state_elems * sizeof(double)) return fail(HYDRO_ERR_NOMEM, "state buffer too small");
+  if (scratch_bytes < g.scratch_bytes) return fail(HYDRO_ERR_NOMEM, "scratch buffer too small");
+
+  hydro_handle* h = new hydro_handle();
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  h->boxes = g.boxes;
+  h->state_bytes = state_bytes;
+  h->scratch_bytes = scratch_bytes;
+  char* scratch = static_cast<char*>(scratch_dev);
+  Plan& p = h->plan;
+  p.nboxes = nboxes;
+  p.boxes = h->boxes.data();
+  p.dboxes = reinterpret_cast<DevBox*>(scratch);
+  p.rt = reinterpret_cast<BoxRt*>(scratch + g.table_bytes);
+  p.state = static_cast<double*>(state_dev);
+  p.work = reinterpret_cast<double*>(scratch + g.head_bytes);
+  p.work_elems = g.work_elems;
+  p.max_interior = 0;
+  p.max_ghosted = 0;
+  for (int a = 0; a < 3; a++) p.max_n[a] = 0;
+
+  std::vector<DevBox> table(nboxes);
+  for (int i = 0; i < nboxes; i++) {
+    const HostBox& hb = h->boxes[i];
+    DevBox& db = table[i];
+    memset(&db, 0, sizeof db);
+    db.n[0] = hb.d.nx;
+    db.n[1] = hb.d.ny;
+    db.n[2] = hb.d.nz;
+    db.precision = hb.d.precision;
+    db.s[0] = 1;
+    db.s[1] = hb.pitch;
+    db.s[2] = hb.plane;
+    db.vs = hb.vs;
+    db.state_off = hb.state_off;
+    db.work_off = hb.work_off;
+    db.stage_off = hb.stage_off;
+    const double dx[3] = {hb.d.dx, hb.d.dy, hb.d.dz};
+    for (int a = 0; a < 3; a++) {
+      db.dx[a] = dx[a];
+      db.idx[a] = 1.0 / dx[a];
+      p.max_n[a] = std::max(p.max_n[a], db.n[a]);
+    }
+    db.gamma = hb.d.gamma;
+    db.igm1 = 1.0 / (hb.d.gamma - 1.0);
+    db.cfl = hb.d.cfl;
+    for (int f = 0; f < 6; f++) db.bc[f] = hb.d.bc[f];
+    p.max_interior = std::max(p.max_interior, hb.interior);
+    p.max_ghosted = std::max(p.max_ghosted, hb.vs);
+  }
+  e = cudaMemcpy(p.dboxes, table.data(), sizeof(DevBox) * nboxes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p.rt, 0, sizeof(BoxRt) * nboxes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "hydro_alloc: writing the box table");
+  }
+  *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_free(hydro_handle* h) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  delete h;
+  return HYDRO_OK;
+}
+
+int hydro_fill_ghosts(hydro_handle* h, void* stream) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  int rc = check_device(h);
+  if (rc) return rc;
+  return launched(run_stage(h, hydro::ST_FILL, static_cast<cudaStream_t>(stream)), "fill_ghosts launch");
+}
+
+int hydro_compute_dt(hydro_handle* h, double* dt_dev, void* stream) {
+  if (!h || !dt_dev) return fail(HYDRO_ERR_INVALID, "null handle or dt pointer");
+  int rc = check_device(h);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = run_stage(h, hydro::ST_PRIM, s);
+  if (e == cudaSuccess) e = run_stage(h, hydro::ST_DT, s, nullptr, dt_dev, 0);
+  return launched(e, "compute_dt launch");
+}
+
+int hydro_step(hydro_handle* h, const double* dt_dev, int nsteps, void* stream) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  if (nsteps < 0) return fail(HYDRO_ERR_INVALID, "nsteps must be >= 0");
+  int rc = check_device(h);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < nsteps; i++) {
+    cudaError_t e = cudaSuccess;
+    for (int st = hydro::ST_FILL; st < hydro::NSTAGES && e == cudaSuccess; st++) {
+      if (st == hydro::ST_DT) e = run_stage(h, hydro::ST_DT, s, dt_dev, nullptr, 1);
+      else e = run_stage(h, static_cast<hydro::Stage>(st), s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+  }
+  return HYDRO_OK;
+}
+
+int hydro_sync(hydro_handle* h, void* stream) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  int rc = check_device(h);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_sync");
+  const int n = h->plan.nboxes;
+  std::vector<BoxRt> rt(n);
+  e = cudaMemcpy(rt.data(), h->plan.rt, sizeof(BoxRt) * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_sync: reading status");
+  int first = -1;
+  for (int i = 0; i < n; i++) {
+    if (rt[i].status && first < 0) first = i;
+  }
+  if (first < 0) return HYDRO_OK;
+  for (int i = 0; i < n; i++) {
+    if (rt[i].status) {
+      e = cudaMemset(&h->plan.rt[i].status, 0, sizeof(unsigned));
+      if (e != cudaSuccess) return cuda_fail(e, "hydro_sync: clearing status");
+    }
+  }
+  char buf[160];
+  snprintf(buf, sizeof buf, "box %d: nonphysical state (rho <= 0, p <= 0 or NaN) after step %u", first,
+           rt[first].steps);
+  return fail(HYDRO_ERR_NONPHYSICAL, buf);
+}
+
+int hydro_get_time(hydro_handle* h, double* time_host, void* stream) {
+  if (!h || !time_host) return fail(HYDRO_ERR_INVALID, "null argument");
+  int rc = check_device(h);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_get_time");
+  const int n = h->plan.nboxes;
+  std::vector<BoxRt> rt(n);
+  e = cudaMemcpy(rt.data(), h->plan.rt, sizeof(BoxRt) * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_get_time: reading times");
+  for (int i = 0; i < n; i++) time_host[i] = rt[i].time;
+  return HYDRO_OK;
+}
+
+int hydro_upload(hydro_handle* h, const double* state_host, size_t bytes, void* stream) {
+  if (!h || !state_host) return fail(HYDRO_ERR_INVALID, "null argument");
+  int rc = check_device(h);
+  if (rc) return rc;
+  size_t need = 0;
+  for (const HostBox& hb : h->boxes) need += 5 * (size_t)hb.interior * sizeof(double);
+  if (bytes != need) return fail(HYDRO_ERR_INVALID, "upload size does not match the boxes' interiors");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h->plan.work, state_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = hydro::launch_scatter(h->plan, h->plan.work, s);
+  h->launches += 1;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return launched(e, "hydro_upload");
+}
+
+int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stream) {
+  if (!h || !state_host) return fail(HYDRO_ERR_INVALID, "null argument");
+  int rc = check_device(h);
+  if (rc) return rc;
+  size_t need = 0;
+  for (const HostBox& hb : h->boxes) need += 5 * (size_t)hb.interior * sizeof(double);
+  if (bytes != need) return fail(HYDRO_ERR_INVALID, "download size does not match the boxes' interiors");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = hydro::launch_gather(h->plan, h->plan.work, s);
+  h->launches += 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(state_host, h->plan.work, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return launched(e, "hydro_download");
+}
+
+int hydro_kernel_launches(hydro_handle* h, int64_t* count) {
+  if (!h || !count) return fail(HYDRO_ERR_INVALID, "null argument");
+  *count = h->launches;
+  return HYDRO_OK;
+}
+
+int hydro_profile_begin(hydro_handle* h) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  h->rec_stage.clear();
+  h->profiling = true;
+  return HYDRO_OK;
+}
+
+int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, int* nstages) {
+  if (!h || !nstages || (max_stages > 0 && !out)) return fail(HYDRO_ERR_INVALID, "null argument");
+  h->profiling = false;
+  double ms[hydro::NSTAGES] = {0};
+  long long n[hydro::NSTAGES] = {0};
+  for (size_t r = 0; r < h->rec_stage.size(); r++) {
+    cudaError_t e = cudaEventSynchronize(h->events[2 * r + 1]);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, h->events[2 * r], h->events[2 * r + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "hydro_profile_end");
+    ms[h->rec_stage[r]] += t;
+    n[h->rec_stage[r]] += hydro::STAGE_KERNELS[h->rec_stage[r]];
+  }
+  h->rec_stage.clear();
+  *nstages = hydro::NSTAGES;
+  for (int s = 0; s < hydro::NSTAGES && s < max_stages; s++) {
+    memset(&out[s], 0, sizeof out[s]);
+    snprintf(out[s].name, sizeof out[s].name, "%s", hydro::STAGE_NAMES[s]);
+    out[s].launches = n[s];
+    out[s].total_ms = ms[s];
+  }
+  return HYDRO_OK;
+}
+
+}  // extern "C"

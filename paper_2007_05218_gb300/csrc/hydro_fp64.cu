@@ -1,0 +1,686 @@
+// FP64 kernels of the unsplit PPM/CTU/HLLC update, one kernel per stage with
+// the intermediates in HBM scratch.
+//
+// Design for GB300: the update costs thousands of FP64 operations per zone
+// and GB300's FP64 pipe is narrow, while HBM bandwidth is plentiful.  So every
+// quantity is computed once and parked in HBM rather than recomputed by
+// neighbouring threads: the stage kernels read their stencil from scratch
+// fields laid out like the state (x fastest, coalesced across a warp).
+//
+// Stages (paper §3: limited slopes from neighbours, then a polynomial
+// reconstruction; the published methods are cited per stage):
+//   k_fill       ghost zones from the boundary conditions (x, then y, then z)
+//   k_prim       conserved -> primitive + EOS; per-box max signal speed for dt
+//   k_dt         dt = cfl / max((|u_d|+c)/dx_d)
+//   k_flatten    CW84 §4 shock flattening coefficient (max over directions)
+//   k_trace      CW84 PPM parabolas + characteristic tracing -> face states
+//   k_riemann    HLLC normal fluxes F0_d on the extended face region
+//   k_ctu1       3D CTU stage 1: dt/(3dx_e) transverse corrections + HLLC
+//   k_ctu2       3D CTU stage 2: dt/(2dx) corrections + HLLC -> final fluxes
+//   k_update     conservative flux-divergence update + physicality flag
+#include <algorithm>
+#include <cmath>
+
+#include "hydro_internal.cuh"
+
+namespace hydro {
+namespace {
+
+constexpr int TPB = 128;
+
+// slot m of the normal frame of axis D -> x,y,z component (0 rho, 1..3 velocity/momentum, 4 p/E)
+template <int D>
+__device__ __forceinline__ constexpr int comp(int m) {
+  return (m == 0 || m == 4) ? m : 1 + (D + m - 1) % 3;
+}
+
+__device__ __forceinline__ long long zone(const DevBox& b, int i, int j, int k) {
+  return (long long)(i + NG) + (long long)(j + NG) * b.s[1] + (long long)(k + NG) * b.s[2];
+}
+
+// linear thread index -> zone of the region lo[a] .. lo[a]+ext[a]-1 (x fastest)
+__device__ __forceinline__ bool decode(long long t, const int* lo, const int* ext, int* c) {
+  long long vol = (long long)ext[0] * ext[1] * ext[2];
+  if (t >= vol) return false;
+  long long r = t / ext[0];
+  c[0] = lo[0] + (int)(t - r * ext[0]);
+  long long k = r / ext[1];
+  c[1] = lo[1] + (int)(r - k * ext[1]);
+  c[2] = lo[2] + (int)k;
+  return true;
+}
+
+__device__ __forceinline__ long long tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// ----------------------------------------------------------------- ghost fill
+template <int D>
+__global__ void __launch_bounds__(256) k_fill(const DevBox* __restrict__ boxes, double* __restrict__ state) {
+  const DevBox& b = boxes[blockIdx.y];
+  int lo[3], ext[3], c[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (a == D) { lo[a] = 0; ext[a] = 2 * NG; }
+    else if (a < D) { lo[a] = -NG; ext[a] = b.n[a] + 2 * NG; }
+    else { lo[a] = 0; ext[a] = b.n[a]; }
+  }
+  if (!decode(tid(), lo, ext, c)) return;
+  const int l = c[D], n = b.n[D];
+  const int side = l < NG ? 0 : 1;
+  const int m = side == 0 ? NG - l : l - NG + 1;  // depth 1..NG
+  const int bc = b.bc[2 * D + side];
+  int src;
+  if (bc == HYDRO_BC_PERIODIC) src = side == 0 ? n - m : m - 1;
+  else if (bc == HYDRO_BC_OUTFLOW) src = side == 0 ? 0 : n - 1;
+  else src = side == 0 ? m - 1 : n - m;
+  c[D] = side == 0 ? -m : n - 1 + m;
+  const long long zg = zone(b, c[0], c[1], c[2]);
+  c[D] = src;
+  const long long zs = zone(b, c[0], c[1], c[2]);
+  double* U = state + b.state_off;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    double val = U[v * b.vs + zs];
+    if (bc == HYDRO_BC_REFLECT && v == 1 + D) val = -val;
+    U[v * b.vs + zg] = val;
+  }
+}
+
+// ------------------------------------------------- conserved -> primitive, dt
+__global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, const double* __restrict__ state,
+                                              double* __restrict__ work, BoxRt* __restrict__ rt) {
+  const int bi = blockIdx.y;
+  const DevBox& b = boxes[bi];
+  int lo[3] = {-NG, -NG, -NG};
+  int ext[3] = {b.n[0] + 2 * NG, b.n[1] + 2 * NG, b.n[2] + 2 * NG};
+  int c[3];
+  unsigned long long sbits = 0ull;
+  if (decode(tid(), lo, ext, c)) {
+    const long long Z = zone(b, c[0], c[1], c[2]);
+    const long long vs = b.vs;
+    const double* U = state + b.state_off;
+    double* W = work + b.work_off;
+    double rho = U[Z];
+    if (rho < SMALL_DENS) rho = SMALL_DENS;
+    const double ir = 1.0 / rho;
+    const double u = U[vs + Z] * ir, v = U[2 * vs + Z] * ir, w = U[3 * vs + Z] * ir;
+    double p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
+    if (p < SMALL_PRES) p = SMALL_PRES;
+    const double cs = sqrt(b.gamma * p * ir);
+    W[Z] = rho;
+    W[vs + Z] = u;
+    W[2 * vs + Z] = v;
+    W[3 * vs + Z] = w;
+    W[4 * vs + Z] = p;
+    W[FLD_C * vs + Z] = cs;
+    if (c[0] >= 0 && c[0] < b.n[0] && c[1] >= 0 && c[1] < b.n[1] && c[2] >= 0 && c[2] < b.n[2]) {
+      double s = fmax(fmax((fabs(u) + cs) * b.idx[0], (fabs(v) + cs) * b.idx[1]), (fabs(w) + cs) * b.idx[2]);
+      sbits = (unsigned long long)__double_as_longlong(s);
+    }
+  }
+  // non-negative doubles order like their bit patterns: reduce as integers
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, sbits, off);
+    sbits = o > sbits ? o : sbits;
+  }
+  if ((threadIdx.x & 31) == 0 && sbits) atomicMax(&rt[bi].smax, sbits);
+}
+
+__global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, int nboxes,
+                     const double* __restrict__ dt_in, double* __restrict__ dt_out, int advance) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nboxes; b += gridDim.x * blockDim.x) {
+    const double smax = __longlong_as_double((long long)rt[b].smax);
+    const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
+    rt[b].smax = 0ull;
+    rt[b].dt = dt;
+    if (dt_out) dt_out[b] = dt;
+    if (advance) {
+      rt[b].time += dt;
+      rt[b].steps += 1u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- flattening
+__device__ __forceinline__ double flat_tilde(const double* __restrict__ p, const double* __restrict__ un,
+                                             long long Z, long long s) {
+  const double pp = p[Z + s], pm = p[Z - s];
+  const double dp1 = pp - pm;
+  if (!(fabs(dp1) > FLAT_EPS * fmin(pp, pm)) || !(un[Z - s] - un[Z + s] > 0.0)) return 0.0;
+  const double dp2 = p[Z + 2 * s] - p[Z - 2 * s];
+  if (dp2 == 0.0) return 0.0;
+  return fmin(1.0, fmax(0.0, FLAT_OMEGA2 * (dp1 / dp2 - FLAT_OMEGA1)));
+}
+
+__global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  const double* p = W + 4 * b.vs;
+  double f = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const double* un = W + (1 + d) * b.vs;
+    const long long s = b.s[d];
+    const long long sh = p[Z + s] - p[Z - s] >= 0.0 ? s : -s;
+    f = fmax(f, fmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s)));
+  }
+  W[FLD_CHI * b.vs + Z] = f;
+}
+
+// ------------------------------------------------------------- PPM + tracing
+__device__ __forceinline__ double vl_slope(double am, double a0, double ap) {
+  const double dl = a0 - am, dr = ap - a0;
+  if (dl * dr > 0.0) {
+    const double dc = 0.5 * (ap - am);
+    return copysign(fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr))), dc);
+  }
+  return 0.0;
+}
+
+// CW84 eqs. 1.6-1.10 on the five-zone stencil a[0..4] (zone i = a[2]), then flattening
+__device__ __forceinline__ void parabola(const double* a, double f, double& L, double& R) {
+  const double dm1 = vl_slope(a[0], a[1], a[2]);
+  const double d0 = vl_slope(a[1], a[2], a[3]);
+  const double dp1 = vl_slope(a[2], a[3], a[4]);
+  const double a0 = a[2];
+  L = a[1] + 0.5 * (a0 - a[1]) - (d0 - dm1) * (1.0 / 6.0);
+  R = a0 + 0.5 * (a[3] - a0) - (dp1 - d0) * (1.0 / 6.0);
+  if ((R - a0) * (a0 - L) <= 0.0) {
+    L = a0;
+    R = a0;
+  } else {
+    const double dA = R - L;
+    const double t1 = dA * (a0 - 0.5 * (L + R));
+    const double t2 = dA * dA * (1.0 / 6.0);
+    if (t1 > t2) L = 3.0 * a0 - 2.0 * R;
+    else if (-t2 > t1) R = 3.0 * a0 - 2.0 * L;
+  }
+  L = f * a0 + (1.0 - f) * L;
+  R = f * a0 + (1.0 - f) * R;
+}
+
+template <int D>
+__device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__ W, long long Z, double dtdx) {
+  const long long vs = b.vs, s = b.s[D];
+  double a0[5], aL[5], aR[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    const double* src = W + comp<D>(m) * vs + Z;
+    double a[5];
+#pragma unroll
+    for (int o = 0; o < 5; o++) a[o] = src[(o - 2) * s];
+    a0[m] = a[2];
+    parabola(a, W[FLD_CHI * vs + Z], aL[m], aR[m]);
+  }
+  double dA[5], a6[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    dA[m] = aR[m] - aL[m];
+    a6[m] = 6.0 * (a0[m] - 0.5 * (aL[m] + aR[m]));
+  }
+  const double cs = W[FLD_C * vs + Z];
+  const double rho = a0[0], u = a0[1];
+  const double ic = 1.0 / cs;
+  const double rc = 0.5 * rho * ic;   // rho / 2c
+  const double i2c2 = 0.5 * ic * ic;  // 1 / 2c^2
+  const double ic2 = ic * ic;         // 1 / c^2
+  const double cr = cs / rho;         // c / rho
+  const double c2 = cs * cs;
+  const double lm = u - cs, lp = u + cs;
+
+  double out[5];
+  // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
+  if (lp > 0.0) {
+    double sg = lp * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
+    double ref[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * a6[m]);
+    double bm = 0.0, b0 = 0.0;
+    out[2] = ref[2];
+    out[3] = ref[3];
+    if (lm > 0.0) {
+      sg = lm * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
+      const double du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * a6[1]));
+      const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      bm = -rc * du + i2c2 * dp;
+    }
+    if (u > 0.0) {
+      sg = u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
+      const double dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * a6[0]));
+      const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      b0 = dr - ic2 * dp;
+      out[2] = aR[2] - h1 * (dA[2] - h2 * a6[2]);
+      out[3] = aR[3] - h1 * (dA[3] - h2 * a6[3]);
+    }
+    out[0] = ref[0] - (bm + b0);
+    out[1] = ref[1] + cr * bm;
+    out[4] = ref[4] - c2 * bm;
+  } else {
+#pragma unroll
+    for (int m = 0; m < 5; m++) out[m] = a0[m];
+  }
+  if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
+  if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+#pragma unroll
+  for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
+
+  // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
+  if (lm < 0.0) {
+    double sg = -lm * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
+    double ref[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * a6[m]);
+    double bp = 0.0, b0 = 0.0;
+    out[2] = ref[2];
+    out[3] = ref[3];
+    if (lp < 0.0) {
+      sg = -lp * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
+      const double du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * a6[1]));
+      const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      bp = rc * du + i2c2 * dp;
+    }
+    if (u < 0.0) {
+      sg = -u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
+      const double dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * a6[0]));
+      const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      b0 = dr - ic2 * dp;
+      out[2] = aL[2] + h1 * (dA[2] + h2 * a6[2]);
+      out[3] = aL[3] + h1 * (dA[3] + h2 * a6[3]);
+    }
+    out[0] = ref[0] - (b0 + bp);
+    out[1] = ref[1] - cr * bp;
+    out[4] = ref[4] - c2 * bp;
+  } else {
+#pragma unroll
+    for (int m = 0; m < 5; m++) out[m] = a0[m];
+  }
+  if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
+  if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+#pragma unroll
+  for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
+}
+
+__global__ void __launch_bounds__(TPB) k_trace(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
+                                               double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  const double dt = rt[blockIdx.y].dt;
+  switch (blockIdx.z) {
+    case 0: trace_zone<0>(b, W, Z, dt * b.idx[0]); break;
+    case 1: trace_zone<1>(b, W, Z, dt * b.idx[1]); break;
+    default: trace_zone<2>(b, W, Z, dt * b.idx[2]); break;
+  }
+}
+
+// ----------------------------------------------------------------------- HLLC
+// Normal-frame states (rho, u_n, u_t1, u_t2, p) -> normal-frame flux.
+// Toro, Spruce & Speares 1994 with Roe-averaged bounds (Batten et al. 1997),
+// Davis bounds when the Roe sound speed is not real.  Only the star state on
+// the side of the contact that contains x/t = 0 is formed.
+__device__ __forceinline__ void hllc(const double* L, const double* R, double gamma, double igm1, double* F) {
+  const double gm1 = gamma - 1.0;
+  const double rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
+  const double rr = R[0], ur = R[1], vr = R[2], wr = R[3], pr = R[4];
+  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double El = pl * igm1 + 0.5 * rl * (ul * ul + vl * vl + wl * wl);
+  const double Er = pr * igm1 + 0.5 * rr * (ur * ur + vr * vr + wr * wr);
+  const double cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+  const double sl = sqrt(rl), sr = sqrt(rr);
+  const double iw = 1.0 / (sl + sr);
+  const double wgl = sl * iw, wgr = sr * iw;
+  const double ut = wgl * ul + wgr * ur;
+  const double vt = wgl * vl + wgr * vr;
+  const double wt = wgl * wl + wgr * wr;
+  const double Ht = wgl * ((El + pl) * irl) + wgr * ((Er + pr) * irr);
+  const double ct2 = gm1 * (Ht - 0.5 * (ut * ut + vt * vt + wt * wt));
+  double SL, SR;
+  if (ct2 > 0.0) {
+    const double ct = sqrt(ct2);
+    SL = fmin(ul - cl, ut - ct);
+    SR = fmax(ur + cr, ut + ct);
+  } else {
+    SL = fmin(ul - cl, ur - cr);
+    SR = fmax(ul + cl, ur + cr);
+  }
+  const double ml = rl * (SL - ul), mr = rr * (SR - ur);
+  const double Ss = (pr - pl + ml * ul - mr * ur) / (ml - mr);
+  const bool left = Ss >= 0.0;
+  const double rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
+  const double pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
+  const double irK = left ? irl : irr;
+  const double mu = rK * uK;
+  F[0] = mu;
+  F[1] = mu * uK + pK;
+  F[2] = mu * vK;
+  F[3] = mu * wK;
+  F[4] = (EK + pK) * uK;
+  const bool supersonic = left ? (SL >= 0.0) : (SR <= 0.0);
+  if (!supersonic) {
+    const double fac = mK / (SK - Ss);
+    const double eK = EK * irK + (Ss - uK) * (Ss + pK / mK);
+    F[0] += SK * (fac - rK);
+    F[1] += SK * (fac * Ss - mu);
+    F[2] += SK * (fac * vK - rK * vK);
+    F[3] += SK * (fac * wK - rK * wK);
+    F[4] += SK * (fac * eK - EK);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void load_face_states(const double* __restrict__ W, long long vs, long long Z, long long sD,
+                                                 double* qL, double* qR) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    qL[m] = W[(FLD_QP + 5 * D + m) * vs + Z - sD];
+    qR[m] = W[(FLD_QM + 5 * D + m) * vs + Z];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void store_flux(double* __restrict__ dst, long long vs, long long Z, const double* Fn) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) dst[comp<D>(m) * vs + Z] = Fn[m];
+}
+
+template <int D>
+__device__ __forceinline__ void riemann_face(const DevBox& b, double* __restrict__ W, long long Z) {
+  double qL[5], qR[5], Fn[5];
+  load_face_states<D>(W, b.vs, Z, b.s[D], qL, qR);
+  hllc(qL, qR, b.gamma, b.igm1, Fn);
+  store_flux<D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
+}
+
+__global__ void __launch_bounds__(TPB) k_riemann(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  const int d = blockIdx.z;
+  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
+  lo[d] = 0;
+  ext[d] = b.n[d] + 1;
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  switch (d) {
+    case 0: riemann_face<0>(b, W, Z); break;
+    case 1: riemann_face<1>(b, W, Z); break;
+    default: riemann_face<2>(b, W, Z); break;
+  }
+}
+
+// ------------------------------------------------------------ CTU corrections
+// Face state q (normal frame of D) of the zone Z -> conserved, minus
+// fac_t * (flux difference across zone Z along stride s_t) for each term t,
+// -> primitive.  A result with rho <= 0 or p <= 0 keeps the uncorrected state.
+template <int D, int NT>
+__device__ __forceinline__ void correct(double* q, const double* const* Fb, const long long* st, const double* fac,
+                                        long long vs, long long Z, double gamma, double igm1) {
+  double U[5];
+  U[0] = q[0];
+  U[1] = q[0] * q[1];
+  U[2] = q[0] * q[2];
+  U[3] = q[0] * q[3];
+  U[4] = q[4] * igm1 + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    const long long off = comp<D>(m) * vs + Z;
+#pragma unroll
+    for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * (Fb[t][off + st[t]] - Fb[t][off]);
+  }
+  if (U[0] > 0.0) {
+    const double ir = 1.0 / U[0];
+    const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const double p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w));
+    if (p > 0.0) {
+      q[0] = U[0];
+      q[1] = u;
+      q[2] = v;
+      q[3] = w;
+      q[4] = p < SMALL_PRES ? SMALL_PRES : p;
+    }
+  }
+}
+
+constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
+
+template <int D, int E>
+__device__ __forceinline__ void ctu1_face(const DevBox& b, double* __restrict__ W, long long Z, double dt) {
+  const long long vs = b.vs, sD = b.s[D];
+  const double igm1 = b.igm1;
+  double qL[5], qR[5], Fn[5];
+  load_face_states<D>(W, vs, Z, sD, qL, qR);
+  const double* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
+  const long long st[1] = {b.s[E]};
+  const double fac[1] = {dt * b.idx[E] * (1.0 / 3.0)};
+  correct<D, 1>(qL, Fb, st, fac, vs, Z - sD, b.gamma, igm1);
+  correct<D, 1>(qR, Fb, st, fac, vs, Z, b.gamma, igm1);
+  hllc(qL, qR, b.gamma, igm1, Fn);
+  store_flux<D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
+}
+
+__global__ void __launch_bounds__(TPB) k_ctu1(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
+                                              double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  const int p = blockIdx.z;  // pair slot: xy xz yx yz zx zy
+  const int d = p / 2, r = p % 2;
+  const int e = r == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);
+  const int f = 3 - d - e;
+  int lo[3], ext[3], c[3];
+  lo[d] = 0; ext[d] = b.n[d] + 1;
+  lo[e] = 0; ext[e] = b.n[e];
+  lo[f] = -1; ext[f] = b.n[f] + 2;
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  const double dt = rt[blockIdx.y].dt;
+  switch (p) {
+    case 0: ctu1_face<0, 1>(b, W, Z, dt); break;
+    case 1: ctu1_face<0, 2>(b, W, Z, dt); break;
+    case 2: ctu1_face<1, 0>(b, W, Z, dt); break;
+    case 3: ctu1_face<1, 2>(b, W, Z, dt); break;
+    case 4: ctu1_face<2, 0>(b, W, Z, dt); break;
+    default: ctu1_face<2, 1>(b, W, Z, dt); break;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void ctu2_face(const DevBox& b, double* __restrict__ W, long long Z, double dt) {
+  constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
+  const long long vs = b.vs, sD = b.s[D];
+  const double igm1 = b.igm1;
+  double qL[5], qR[5], Fn[5];
+  load_face_states<D>(W, vs, Z, sD, qL, qR);
+  const double* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
+  const long long st[2] = {b.s[E], b.s[F]};
+  const double fac[2] = {0.5 * dt * b.idx[E], 0.5 * dt * b.idx[F]};
+  correct<D, 2>(qL, Fb, st, fac, vs, Z - sD, b.gamma, igm1);
+  correct<D, 2>(qR, Fb, st, fac, vs, Z, b.gamma, igm1);
+  hllc(qL, qR, b.gamma, igm1, Fn);
+  store_flux<D>(W + (FLD_F + 5 * D) * vs, vs, Z, Fn);
+}
+
+__global__ void __launch_bounds__(TPB) k_ctu2(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
+                                              double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  const int d = blockIdx.z;
+  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
+  ext[d] = b.n[d] + 1;
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  const double dt = rt[blockIdx.y].dt;
+  switch (d) {
+    case 0: ctu2_face<0>(b, W, Z, dt); break;
+    case 1: ctu2_face<1>(b, W, Z, dt); break;
+    default: ctu2_face<2>(b, W, Z, dt); break;
+  }
+}
+
+// --------------------------------------------------------------------- update
+__global__ void __launch_bounds__(256) k_update(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt,
+                                                double* __restrict__ state, const double* __restrict__ work) {
+  const int bi = blockIdx.y;
+  const DevBox& b = boxes[bi];
+  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  const long long vs = b.vs;
+  double* U = state + b.state_off;
+  const double* W = work + b.work_off;
+  const double dt = rt[bi].dt;
+  const double dtdx[3] = {dt * b.idx[0], dt * b.idx[1], dt * b.idx[2]};
+  double nu[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    double val = U[v * vs + Z];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double* F = W + (FLD_F + 5 * d + v) * vs;
+      val = val - dtdx[d] * (F[Z + b.s[d]] - F[Z]);
+    }
+    nu[v] = val;
+    U[v * vs + Z] = val;
+  }
+  const double kin = 0.5 * (nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3]) / nu[0];
+  const double p = (b.gamma - 1.0) * (nu[4] - kin);
+  if (!(nu[0] > 0.0) || !(p > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+}
+
+// ----------------------------------------------------- host staging transfers
+__global__ void __launch_bounds__(256) k_scatter(const DevBox* __restrict__ boxes, double* __restrict__ state,
+                                                 const double* __restrict__ stage) {
+  const DevBox& b = boxes[blockIdx.y];
+  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  const long long N = (long long)b.n[0] * b.n[1] * b.n[2];
+  const long long src = b.stage_off + ((long long)c[2] * b.n[1] + c[1]) * b.n[0] + c[0];
+#pragma unroll
+  for (int v = 0; v < 5; v++) state[b.state_off + v * b.vs + Z] = stage[src + v * N];
+}
+
+__global__ void __launch_bounds__(256) k_gather(const DevBox* __restrict__ boxes, const double* __restrict__ state,
+                                                double* __restrict__ stage) {
+  const DevBox& b = boxes[blockIdx.y];
+  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  const long long N = (long long)b.n[0] * b.n[1] * b.n[2];
+  const long long dst = b.stage_off + ((long long)c[2] * b.n[1] + c[1]) * b.n[0] + c[0];
+#pragma unroll
+  for (int v = 0; v < 5; v++) stage[dst + v * N] = state[b.state_off + v * b.vs + Z];
+}
+
+// max over boxes of the volume of a region whose extent on axis a is n[a] + add[a]
+long long max_volume(const Plan& p, int a0, int a1, int a2) {
+  long long m = 0;
+  for (int i = 0; i < p.nboxes; i++) {
+    const hydro_box_desc& d = p.boxes[i].d;
+    long long v = (long long)(d.nx + a0) * (d.ny + a1) * (d.nz + a2);
+    if (v > m) m = v;
+  }
+  return m;
+}
+
+// max over boxes and axis orders of a face region: axis a has n+1 faces,
+// axis e is interior, axis f has n + fext zones (fext = 2 for CTU stage 1, 0 for stage 2)
+long long max_volume_faces(const Plan& p, int fext) {
+  long long m = 0;
+  for (int i = 0; i < p.nboxes; i++) {
+    const hydro_box_desc& d = p.boxes[i].d;
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; a++)
+      for (int e = 0; e < 3; e++) {
+        if (e == a) continue;
+        const int f = 3 - a - e;
+        const long long v = (long long)(n[a] + 1) * n[e] * (n[f] + fext);
+        if (v > m) m = v;
+      }
+  }
+  return m;
+}
+
+dim3 grid_for(long long vol, int tpb, int nboxes, int z = 1) {
+  long long bx = (vol + tpb - 1) / tpb;
+  if (bx < 1) bx = 1;
+  return dim3((unsigned)bx, (unsigned)nboxes, (unsigned)z);
+}
+
+}  // namespace
+
+const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "trace",
+                                           "riemann", "ctu1", "ctu2", "update"};
+const int STAGE_KERNELS[NSTAGES] = {3, 1, 1, 1, 1, 1, 1, 1, 1};
+
+cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
+                         int advance) {
+  switch (st) {
+    case ST_FILL: {
+      long long vx = 0, vy = 0, vz = 0;
+      for (int i = 0; i < p.nboxes; i++) {
+        const hydro_box_desc& d = p.boxes[i].d;
+        vx = std::max(vx, (long long)2 * NG * d.ny * d.nz);
+        vy = std::max(vy, (long long)2 * NG * (d.nx + 2 * NG) * d.nz);
+        vz = std::max(vz, (long long)2 * NG * (d.nx + 2 * NG) * (d.ny + 2 * NG));
+      }
+      k_fill<0><<<grid_for(vx, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
+      k_fill<1><<<grid_for(vy, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
+      k_fill<2><<<grid_for(vz, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
+      break;
+    }
+    case ST_PRIM:
+      k_prim<<<grid_for(max_volume(p, 2 * NG, 2 * NG, 2 * NG), 256, p.nboxes), 256, 0, stream>>>(
+          p.dboxes, p.state, p.work, p.rt);
+      break;
+    case ST_DT:
+      k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
+      break;
+    case ST_FLATTEN:
+      k_flatten<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes), TPB, 0, stream>>>(p.dboxes, p.work);
+      break;
+    case ST_TRACE:
+      k_trace<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
+      break;
+    case ST_RIEMANN: {
+      // normal faces: axis d has n+1 faces, both transverse axes n+2 zones
+      long long vf0 = 0;
+      for (int i = 0; i < p.nboxes; i++) {
+        const hydro_box_desc& d = p.boxes[i].d;
+        const int n[3] = {d.nx, d.ny, d.nz};
+        for (int a = 0; a < 3; a++)
+          vf0 = std::max(vf0, (long long)(n[a] + 1) * (n[(a + 1) % 3] + 2) * (n[(a + 2) % 3] + 2));
+      }
+      k_riemann<<<grid_for(vf0, TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.work);
+      break;
+    }
+    case ST_CTU1:
+      k_ctu1<<<grid_for(max_volume_faces(p, 2), TPB, p.nboxes, 6), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
+      break;
+    case ST_CTU2:
+      k_ctu2<<<grid_for(max_volume_faces(p, 0), TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
+      break;
+    case ST_UPDATE:
+      k_update<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.rt, p.state,
+                                                                                   p.work);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream) {
+  k_scatter<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state, stage);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream) {
+  k_gather<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state, stage);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

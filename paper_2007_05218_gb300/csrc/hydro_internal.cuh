@@ -1,0 +1,117 @@
+// Internal declarations shared by the CUDA translation units of the hydro
+// library (box table, per-box runtime record, scratch field map, launchers).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hydro.h"
+
+namespace hydro {
+
+constexpr int NG = HYDRO_NG;
+
+// Method parameters (floors and CW84 flattening constants).
+constexpr double SMALL_DENS = 1e-12;
+constexpr double SMALL_PRES = 1e-12;
+constexpr double FLAT_EPS = 0.33;
+constexpr double FLAT_OMEGA1 = 0.75;
+constexpr double FLAT_OMEGA2 = 10.0;
+
+// Scratch fields of one box, each a full ghosted-box grid of doubles with the
+// state's pitch/plane strides:
+//   q[5] primitive (rho,u,v,w,p), c sound speed, chi flattening,
+//   qm[d][5] / qp[d][5] traced left-/right-edge states in the normal frame of d
+//   (rho, u_n, u_t1, u_t2, p with t1 = (d+1)%3, t2 = (d+2)%3),
+//   f0[d][5] normal fluxes, f1[pair][5] singly corrected fluxes for the ordered
+//   pairs (d,e) = xy,xz,yx,yz,zx,zy, f[d][5] final fluxes (conserved x,y,z order).
+// Flux of a d-face between zones Z-s_d and Z is stored at zone Z.
+enum Field : int {
+  FLD_Q = 0,
+  FLD_C = 5,
+  FLD_CHI = 6,
+  FLD_QM = 7,
+  FLD_QP = 22,
+  FLD_F0 = 37,
+  FLD_F1 = 52,
+  FLD_F = 82,
+  NFIELDS = 97
+};
+
+// Per-box geometry as the kernels see it (lives in the head of scratch).
+struct DevBox {
+  int n[3];
+  int precision;
+  long long s[3];         // element strides of i, j, k
+  long long vs;           // element stride between fields/variables
+  long long state_off;    // first state element of this box
+  long long work_off;     // first scratch element of this box's fields
+  long long stage_off;    // first element of this box in the compact host staging layout
+  double dx[3];
+  double idx[3];          // 1/dx
+  double gamma;
+  double igm1;            // 1/(gamma-1)
+  double cfl;
+  int bc[6];
+  int pad[2];
+};
+
+// Per-box runtime record (lives in scratch, after the box table).
+struct BoxRt {
+  unsigned long long smax;  // max over interior zones/axes of (|u|+c)/dx, as non-negative double bits
+  double dt;                // time step of the current update
+  double time;              // simulated time advanced so far
+  unsigned int status;      // device error flags (STATUS_*)
+  unsigned int steps;       // updates applied
+};
+
+constexpr unsigned STATUS_NONPHYSICAL = 1u;
+
+// Geometry computed on the host for one box.
+struct HostBox {
+  hydro_box_desc d;
+  long long pitch, plane, vs;
+  long long state_off, work_off, stage_off;
+  long long interior;  // nx*ny*nz
+};
+
+// Host-side plan of a handle.
+struct Plan {
+  int nboxes;
+  HostBox* boxes;      // host array [nboxes]
+  DevBox* dboxes;      // device table (in scratch)
+  BoxRt* rt;           // device runtime records (in scratch)
+  double* state;
+  double* work;        // start of the per-box field area (in scratch)
+  size_t work_elems;   // elements of the field area
+  int max_n[3];        // max interior extent per axis over boxes
+  long long max_ghosted, max_interior;
+};
+
+// Stages of one step, in launch order.  Each stage is one kernel, except the
+// ghost fill (three kernels: x, y, z).
+enum Stage : int {
+  ST_FILL = 0,
+  ST_PRIM,
+  ST_DT,
+  ST_FLATTEN,
+  ST_TRACE,
+  ST_RIEMANN,
+  ST_CTU1,
+  ST_CTU2,
+  ST_UPDATE,
+  NSTAGES
+};
+extern const char* const STAGE_NAMES[NSTAGES];
+extern const int STAGE_KERNELS[NSTAGES];
+
+// Launches one stage for every box of the plan (hydro_fp64.cu), asynchronously
+// on `stream`.  ST_DT uses dt_in[b] when dt_in is not null (else cfl/smax),
+// writes dt_out[b] when dt_out is not null, and advances the per-box time when
+// `advance` is set.
+cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in = nullptr,
+                         double* dt_out = nullptr, int advance = 0);
+cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream);
+cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream);
+
+}  // namespace hydro

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of include/hydro.h (argument marshalling only).
+
+Functions keep the C names (hydro_alloc, hydro_step, ...).  Device buffers are
+torch CUDA tensors (PyTorch supplies memory and streams); every step of the
+update runs in the CUDA library.  There is no CPU fallback: if the library is
+missing or was built for another machine, loading it raises.
+
+`Boxes` is a small convenience owner of the state/scratch tensors and handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HYDRO_OK = 0
+HYDRO_PENDING = 1
+HYDRO_ERR_INVALID = -1
+HYDRO_ERR_NOMEM = -2
+HYDRO_ERR_NONPHYSICAL = -3
+HYDRO_ERR_TIMEOUT = -4
+HYDRO_ERR_CUDA = -5
+HYDRO_BC = {"periodic": 0, "outflow": 1, "reflect": 2}
+HYDRO_FP64 = 0
+HYDRO_MIXED = 1
+HYDRO_NG = 4
+
+EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_free", "hydro_fill_ghosts",
+            "hydro_compute_dt", "hydro_step", "hydro_sync", "hydro_get_time", "hydro_upload",
+            "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
+            "hydro_profile_end", "hydro_last_error")
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class hydro_box_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("ng", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("bc", ctypes.c_int32 * 6), ("precision", ctypes.c_int32)]
+
+
+class hydro_layout(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("pitch", ctypes.c_int64), ("plane", ctypes.c_int64),
+                ("var_stride", ctypes.c_int64)]
+
+
+class hydro_stage_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+
+
+def load(path: str | None = None):
+    """Loads (building first if needed) libhydro_gb300.so; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB_PATH
+        if not os.path.exists(path) or not _build.up_to_date():
+            _build.build()
+        L = ctypes.CDLL(path)
+        D = ctypes.POINTER(hydro_box_desc)
+        i = ctypes.c_int
+        L.hydro_workspace_size.argtypes = [D, i, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]
+        L.hydro_box_layout.argtypes = [D, i, i, ctypes.POINTER(hydro_layout)]
+        L.hydro_alloc.argtypes = [D, i, _VP, _SZ, _VP, _SZ, ctypes.POINTER(_VP)]
+        L.hydro_free.argtypes = [_VP]
+        L.hydro_fill_ghosts.argtypes = [_VP, _VP]
+        L.hydro_compute_dt.argtypes = [_VP, _VP, _VP]
+        L.hydro_step.argtypes = [_VP, _VP, i, _VP]
+        L.hydro_sync.argtypes = [_VP, _VP]
+        L.hydro_get_time.argtypes = [_VP, _VP, _VP]
+        L.hydro_upload.argtypes = [_VP, _VP, _SZ, _VP]
+        L.hydro_download.argtypes = [_VP, _VP, _SZ, _VP]
+        L.hydro_debug_fields.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+        L.hydro_kernel_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
+        L.hydro_profile_begin.argtypes = [_VP]
+        L.hydro_profile_end.argtypes = [_VP, ctypes.POINTER(hydro_stage_time), i, ctypes.POINTER(i)]
+        L.hydro_last_error.restype = ctypes.c_char_p
+        L.hydro_last_error.argtypes = []
+        _lib = L
+        return L
+
+
+def hydro_last_error() -> str:
+    return load().hydro_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise HydroError(rc, hydro_last_error())
+    return rc
+
+
+def _stream(stream) -> int | None:
+    """torch.cuda.Stream, raw handle int, or None (torch's current stream)."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def desc_array(descs):
+    arr = (hydro_box_desc * len(descs))()
+    for k, d in enumerate(descs):
+        arr[k] = d
+    return arr
+
+
+def make_desc(shape, dx, gamma, cfl, bc, precision=HYDRO_FP64) -> hydro_box_desc:
+    d = hydro_box_desc()
+    d.nx, d.ny, d.nz = (int(v) for v in shape)
+    d.ng = HYDRO_NG
+    d.dx, d.dy, d.dz = (float(v) for v in dx)
+    d.gamma = float(gamma)
+    d.cfl = float(cfl)
+    for a in range(6):
+        d.bc[a] = HYDRO_BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+    d.precision = int(precision)
+    return d
+
+
+def desc_of(problem, precision=HYDRO_FP64) -> hydro_box_desc:
+    return make_desc(problem.shape, problem.dx, problem.gamma, problem.cfl, problem.bc, precision)
+
+
+# ---------------------------------------------------------------- C names
+def hydro_workspace_size(descs):
+    arr = desc_array(descs)
+    sb, wb = _SZ(), _SZ()
+    _check(load().hydro_workspace_size(arr, len(descs), ctypes.byref(sb), ctypes.byref(wb)))
+    return sb.value, wb.value
+
+
+def hydro_box_layout(descs, box: int) -> hydro_layout:
+    out = hydro_layout()
+    _check(load().hydro_box_layout(desc_array(descs), len(descs), int(box), ctypes.byref(out)))
+    return out
+
+
+def hydro_debug_fields(descs, box: int):
+    off, nf = ctypes.c_int64(), ctypes.c_int32()
+    _check(load().hydro_debug_fields(desc_array(descs), len(descs), int(box), ctypes.byref(off),
+                                     ctypes.byref(nf)))
+    return off.value, nf.value
+
+
+def hydro_alloc(descs, state, state_bytes, scratch, scratch_bytes) -> int:
+    h = _VP()
+    _check(load().hydro_alloc(desc_array(descs), len(descs), _ptr(state), int(state_bytes), _ptr(scratch),
+                              int(scratch_bytes), ctypes.byref(h)))
+    return h.value
+
+
+def hydro_free(h: int) -> None:
+    _check(load().hydro_free(h))
+
+
+def hydro_fill_ghosts(h: int, stream=None) -> None:
+    _check(load().hydro_fill_ghosts(h, _stream(stream)))
+
+
+def hydro_compute_dt(h: int, dt_dev, stream=None) -> None:
+    _check(load().hydro_compute_dt(h, _ptr(dt_dev), _stream(stream)))
+
+
+def hydro_step(h: int, dt_dev=None, nsteps: int = 1, stream=None) -> None:
+    _check(load().hydro_step(h, _ptr(dt_dev), int(nsteps), _stream(stream)))
+
+
+def hydro_sync(h: int, stream=None) -> int:
+    return _check(load().hydro_sync(h, _stream(stream)))
+
+
+def hydro_get_time(h: int, nboxes: int, stream=None) -> np.ndarray:
+    out = np.zeros(nboxes)
+    _check(load().hydro_get_time(h, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def hydro_upload(h: int, host: np.ndarray, stream=None) -> None:
+    host = np.ascontiguousarray(host, dtype=np.float64)
+    _check(load().hydro_upload(h, host.ctypes.data, host.nbytes, _stream(stream)))
+
+
+def hydro_download(h: int, host: np.ndarray, stream=None) -> None:
+    assert host.dtype == np.float64 and host.flags["C_CONTIGUOUS"]
+    _check(load().hydro_download(h, host.ctypes.data, host.nbytes, _stream(stream)))
+
+
+def hydro_kernel_launches(h: int) -> int:
+    c = ctypes.c_int64()
+    _check(load().hydro_kernel_launches(h, ctypes.byref(c)))
+    return c.value
+
+
+def hydro_profile_begin(h: int) -> None:
+    _check(load().hydro_profile_begin(h))
+
+
+def hydro_profile_end(h: int) -> dict:
+    """{stage name: (kernel launches, total device ms)} in launch order."""
+    buf = (hydro_stage_time * 32)()
+    n = ctypes.c_int()
+    _check(load().hydro_profile_end(h, buf, 32, ctypes.byref(n)))
+    return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(n.value)}
+
+
+# ------------------------------------------------------------ convenience
+class Boxes:
+    """Owns torch-allocated state and scratch for a set of boxes and a handle."""
+
+    def __init__(self, problems_or_descs, device="cuda"):
+        import torch
+        items = list(problems_or_descs)
+        self.descs = [p if isinstance(p, hydro_box_desc) else desc_of(p) for p in items]
+        self.nboxes = len(self.descs)
+        sb, wb = hydro_workspace_size(self.descs)
+        self.state_bytes, self.scratch_bytes = sb, wb
+        self.state = torch.empty((sb + 7) // 8, dtype=torch.float64, device=device)
+        self.scratch = torch.empty((wb + 7) // 8, dtype=torch.float64, device=device)
+        self.layouts = [hydro_box_layout(self.descs, b) for b in range(self.nboxes)]
+        self.h = hydro_alloc(self.descs, self.state, sb, self.scratch, wb)
+        self.dt = torch.zeros(self.nboxes, dtype=torch.float64, device=device)
+        for k, p in enumerate(items):
+            if not isinstance(p, hydro_box_desc):
+                self.set_interior(k, p.U)
+
+    def close(self):
+        if self.h:
+            hydro_free(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, b):
+        d = self.descs[b]
+        return d.nx, d.ny, d.nz
+
+    def state_view(self, b):
+        """[5][nz+2g][ny+2g][nx+2g] strided view of box b's state (ghosts included)."""
+        import torch
+        lay = self.layouts[b]
+        nx, ny, nz = self.shape(b)
+        g = HYDRO_NG
+        return torch.as_strided(self.state, (5, nz + 2 * g, ny + 2 * g, nx + 2 * g),
+                                (lay.var_stride, lay.plane, lay.pitch, 1), lay.offset)
+
+    def field_view(self, b, first, count=1):
+        """Diagnostic view of `count` scratch fields of box b starting at field `first`."""
+        import torch
+        off, nf = hydro_debug_fields(self.descs, b)
+        lay = self.layouts[b]
+        nx, ny, nz = self.shape(b)
+        g = HYDRO_NG
+        return torch.as_strided(self.scratch, (count, nz + 2 * g, ny + 2 * g, nx + 2 * g),
+                                (lay.var_stride, lay.plane, lay.pitch, 1), off + first * lay.var_stride)
+
+    def set_interior(self, b, U):
+        import torch
+        g = HYDRO_NG
+        v = self.state_view(b)
+        v[:, g:-g, g:-g, g:-g] = torch.as_tensor(np.ascontiguousarray(U), device=self.state.device)
+
+    def interior(self, b) -> np.ndarray:
+        g = HYDRO_NG
+        return self.state_view(b)[:, g:-g, g:-g, g:-g].cpu().numpy()
+
+    def ghosted(self, b) -> np.ndarray:
+        return self.state_view(b).cpu().numpy()
+
+    def fill_ghosts(self, stream=None):
+        hydro_fill_ghosts(self.h, stream)
+
+    def compute_dt(self, stream=None):
+        hydro_compute_dt(self.h, self.dt, stream)
+        return self.dt
+
+    def step(self, nsteps=1, dt=None, stream=None):
+        hydro_step(self.h, dt, nsteps, stream)
+
+    def sync(self, stream=None):
+        return hydro_sync(self.h, stream)
+
+    def time(self, stream=None):
+        return hydro_get_time(self.h, self.nboxes, stream)
