@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64 unsplit PPM/CTU/HLLC hydro update on one GB300.
+
+Workload (the metric's FP64 configuration): one 256^3 box with 4 ghost zones,
+periodic, gamma = 5/3, seeded smooth density wave rho = 1 + 0.1 sin(2 pi (x+y+z)),
+velocity (1, 0.5, 0.25), p = 1 + 1e-3 U(-1,1).  One benchmark step is one full
+hydro time step (ghost fill, dt reduction, primitive variables, flattening,
+PPM + characteristic tracing, 12 HLLC solves per zone through the 3D CTU
+corrections, flux-divergence update).  Metric: zone-updates/s = interior
+zones x steps / device time.  The state (0.7 GB) and scratch (14 GB) are far
+larger than L2, so no explicit flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank advances its own replica box (weak scaling, no
+data-path collective: boxes are independent problems).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s (FP64 & mixed <=1e-5 rel L1) + p50/p99 served-solve latency"
+UNIT = "zone-updates/s"
+N_BOX = 256
+
+# FP64 peak for the ALU roofline: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz.
+# (GB300 nominal FP64 is 1.25 TFLOP/s; 1.25e12 / (152 x 2.07e9) = 4 flop/clk/SM.)
+FP64_PEAK_FLOPS = 152 * 4 * 2070e6
+
+# Algorithmic FP64 flops (add/sub, mul, div, sqrt; each counts 1) per unit of
+# work of each stage, counted by the oracle (python -m oracle.count_flops
+# density_wave 256: one step of this workload, every quantity formed once).
+FLOPS_PER_UNIT = {
+    "prim": 16.00, "flatten": 21.00, "trace": 341.01, "riemann": 125.00,
+    "ctu1": 207.00, "ctu2": 237.00, "update": 55.00,
+}
+
+
+# DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
+# stands (k_ctu1, 128^3 density wave: 2.160 GB over 12.88 M faces); a stage
+# missing here has no capture of its current code and reports traffic null.
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": 2.160e9 / 12879360}
+
+
+def units_per_launch(stage: str, n) -> int:
+    """Units of work one launch of `stage` processes on a box of n = (nx, ny, nz)."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    ext = (nx + 2) * (ny + 2) * (nz + 2)
+    nn = (nx, ny, nz)
+    if stage == "prim":
+        return (nx + 8) * (ny + 8) * (nz + 8)
+    if stage == "flatten":
+        return ext
+    if stage == "trace":
+        return 3 * ext
+    if stage == "update":
+        return N
+    tot = 0
+    for d in range(3):
+        e, f = (d + 1) % 3, (d + 2) % 3
+        if stage == "riemann":
+            tot += (nn[d] + 1) * (nn[e] + 2) * (nn[f] + 2)
+        elif stage == "ctu1":
+            tot += (nn[d] + 1) * nn[e] * (nn[f] + 2) + (nn[d] + 1) * nn[f] * (nn[e] + 2)
+        elif stage == "ctu2":
+            tot += (nn[d] + 1) * nn[e] * nn[f]
+    return tot
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def oracle_sample(seconds: float, n: int = 64, min_steps: int = 2, nthreads: int | None = None):
+    """Times the oracle (as it stands) on a density-wave box of n^3 zones with the
+    same recipe; returns (zone-updates/s, steps, threads)."""
+    import oracle
+    from paper_2007_05218_gb300 import inputs
+    threads = nthreads or len(os.sched_getaffinity(0))
+    pr = inputs.density_wave(n, seed=0)
+    box = oracle.box_of(pr)
+    Ug = oracle.embed(pr.U)
+    steps, t0 = 0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < seconds:
+        oracle.fill_ghosts(box, Ug)
+        dt = oracle.compute_dt(box, Ug)
+        rc, _ = oracle.step(box, Ug, dt, nthreads=threads)
+        if rc:
+            raise RuntimeError(f"oracle step failed: {rc}")
+        steps += 1
+    el = time.perf_counter() - t0
+    return n ** 3 * steps / el, steps, threads
+
+
+def run_reference(args, rank: int) -> None:
+    """Reference arm: the FP64 oracle on the host cores, one 64^3 density-wave
+    step (same recipe) per benchmark step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2007_05218_gb300 import inputs
+    threads = len(os.sched_getaffinity(0))
+    n = 64
+    pr = inputs.density_wave(n, seed=0)
+    box = oracle.box_of(pr)
+    Ug = oracle.embed(pr.U)
+
+    def one():
+        oracle.fill_ghosts(box, Ug)
+        dt = oracle.compute_dt(box, Ug)
+        rc, _ = oracle.step(box, Ug, dt, nthreads=threads)
+        if rc:
+            raise RuntimeError(f"oracle step failed: {rc}")
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el
+    sample = f"density wave {n}^3 (same recipe as the 256^3 workload), one oracle step per benchmark step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"density_wave_{N_BOX}", "box": [N_BOX] * 3, "ghosts": 4,
+                                        "gamma": 5.0 / 3.0, "bc": "periodic", "cfl": 0.5, "precision": "fp64",
+                                        "sampled_as": f"{n}^3 box of the same recipe per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ main arm
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--box", type=int, default=N_BOX, help="box edge (default 256; smaller only for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2007_05218_gb300 import hydro, inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    nb = args.box
+    n = (nb, nb, nb)
+    N = nb ** 3
+    pr = inputs.density_wave(nb, seed=rank)
+    B = hydro.Boxes([pr])
+    B_state_gb, B_scratch_gb = B.state_bytes / 1e9, B.scratch_bytes / 1e9
+    stream = torch.cuda.current_stream()
+    B.step(args.warmup)
+    B.sync()
+
+    # ---- device-timed region: K steps
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    launches0 = hydro.hydro_kernel_launches(B.h)
+    hydro.hydro_profile_begin(B.h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hydro.hydro_step(B.h, None, 1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = hydro.hydro_profile_end(B.h)
+    launches = hydro.hydro_kernel_launches(B.h) - launches0
+    B.sync()  # raises on a nonphysical state
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = t.item()
+    value = world * N * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI: pinned host IC -> K steps -> host result
+    nbytes = pr.U.nbytes
+    host_in = torch.empty(pr.U.size, dtype=torch.float64, pin_memory=True)
+    host_in.numpy()[:] = pr.U.ravel()
+    host_out = torch.empty(pr.U.size, dtype=torch.float64, pin_memory=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hydro.hydro_upload(B.h, host_in.numpy(), stream)
+    hydro.hydro_step(B.h, None, args.steps, stream)
+    hydro.hydro_download(B.h, host_out.numpy(), stream)
+    e2e_s = time.perf_counter() - t0
+    B.sync()
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e = {"value": world * N * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+           "what": "hydro_upload of the interior initial state from pinned host memory, K steps, "
+                   "hydro_download of the final interior state (bytes per step = solve bytes / K)"}
+    B.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (live event times of this run)
+    stage_ms = {k: v for k, v in prof.items() if k in FLOPS_PER_UNIT}
+    top = max(stage_ms, key=lambda k: stage_ms[k][1])
+    nlaunch, tot_ms = stage_ms[top]
+    avg_s = tot_ms / nlaunch * 1e-3
+    flops = FLOPS_PER_UNIT[top] * units_per_launch(top, n)
+    achieved = flops / avg_s
+    roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS,
+                "traffic": (TRAFFIC_BYTES_PER_UNIT[top] * units_per_launch(top, n)
+                            if top in TRAFFIC_BYTES_PER_UNIT else None),
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "flops_per_launch": flops}
+    total_flops = sum(FLOPS_PER_UNIT[s] * units_per_launch(s, n) for s in FLOPS_PER_UNIT)
+    step_fp64 = total_flops / (ms / args.steps * 1e-3)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, steps, threads = oracle_sample(10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"density wave 64^3 (same recipe), {steps} oracle steps on {threads} threads"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"density_wave_{nb}", "box": list(n), "ghosts": 4, "gamma": 5.0 / 3.0,
+                   "bc": "periodic", "cfl": 0.5, "precision": "fp64",
+                   "l2": "inputs larger than L2 (state %.1f GB + scratch %.1f GB per box)"
+                         % (B_state_gb, B_scratch_gb),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "fp64_algorithmic_tflops_whole_step": step_fp64 / 1e12,
+        "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
