@@ -142,6 +142,10 @@ cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const do
 
 }  // namespace
 
+namespace hydro {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace hydro
+
 extern "C" {
 
 const char* hydro_last_error(void) { return g_err.c_str(); }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/hydro.h"
@@ -112,6 +113,8 @@ extern const int STAGE_KERNELS[NSTAGES];
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in = nullptr,
                          double* dt_out = nullptr, int advance = 0);
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream);
+// Sets the thread-local message returned by hydro_last_error (hydro_api.cu).
+void set_last_error(const std::string& msg);
 cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream);
 
 }  // namespace hydro

@@ -32,7 +32,7 @@ HYDRO_NG = 4
 EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_free", "hydro_fill_ghosts",
             "hydro_compute_dt", "hydro_step", "hydro_sync", "hydro_get_time", "hydro_upload",
             "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
-            "hydro_profile_end", "hydro_last_error")
+            "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         L.hydro_kernel_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
         L.hydro_profile_begin.argtypes = [_VP]
         L.hydro_profile_end.argtypes = [_VP, ctypes.POINTER(hydro_stage_time), i, ctypes.POINTER(i)]
+        L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
         L.hydro_last_error.restype = ctypes.c_char_p
         L.hydro_last_error.argtypes = []
         _lib = L
@@ -228,6 +229,13 @@ def hydro_profile_end(h: int) -> dict:
     n = ctypes.c_int()
     _check(load().hydro_profile_end(h, buf, 32, ctypes.byref(n)))
     return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(n.value)}
+
+
+def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:
+    """Per-box CFL time steps for states laid out as hydro_box_layout says,
+    without a handle or caller scratch (the library's static scratch is used)."""
+    _check(load().hydro_compute_dt_noalloc(desc_array(descs), len(descs), _ptr(state_dev), _ptr(dt_dev),
+                                           _stream(stream)))
 
 
 # ------------------------------------------------------------ convenience
