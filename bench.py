@@ -41,15 +41,15 @@ FP64_PEAK_FLOPS = 152 * 4 * 2070e6
 # work of each stage, counted by the oracle (python -m oracle.count_flops
 # density_wave 256: one step of this workload, every quantity formed once).
 FLOPS_PER_UNIT = {
-    "prim": 16.00, "flatten": 21.00, "trace": 341.01, "riemann": 125.00,
+    "prim": 16.00, "flatten": 21.00, "slopes": 20.27, "trace": 320.58, "riemann": 125.00,
     "ctu1": 207.00, "ctu2": 237.00, "update": 55.00,
 }
 
 
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
-# stands (k_ctu1, 128^3 density wave: 2.160 GB over 12.88 M faces); a stage
-# missing here has no capture of its current code and reports traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": 2.160e9 / 12879360}
+# stands; a stage missing here has no capture of its current code and reports
+# traffic null.
+TRAFFIC_BYTES_PER_UNIT = {}
 
 
 def units_per_launch(stage: str, n) -> int:
@@ -64,6 +64,8 @@ def units_per_launch(stage: str, n) -> int:
         return ext
     if stage == "trace":
         return 3 * ext
+    if stage == "slopes":
+        return sum((nn[d] + 4) * (nn[(d + 1) % 3] + 2) * (nn[(d + 2) % 3] + 2) for d in range(3))
     if stage == "update":
         return N
     tot = 0

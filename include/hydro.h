@@ -143,13 +143,14 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 /* Diagnostics: where the per-zone intermediates of box `box` live inside the
  * scratch buffer, for stage-by-stage checks.  *offset receives the element
  * (FP64) offset of the box's first field from the start of scratch_dev and
- * *nfields the number of fields (97).  Each field is a ghosted-box grid with
+ * *nfields the number of fields (112).  Each field is a ghosted-box grid with
  * the state's pitch, plane and var_stride (fields are var_stride apart), in
  * this order: primitive q[5] = (rho,u,v,w,p); sound speed c; flattening
  * coefficient chi; left-edge states qm[3][5] and right-edge states qp[3][5]
  * per axis d in the normal frame of d (rho, u_d, u_{d+1}, u_{d+2}, p, axis
  * indices mod 3); normal fluxes f0[3][5]; once-corrected fluxes f1[6][5] for
- * the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes f[3][5].  Fluxes are
+ * the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes f[3][5]; limited
+ * slopes dq[3][5] of the normal-frame variables of each axis.  Fluxes are
  * conserved-variable components; the flux through the low face of zone
  * (i,j,k) along d is stored at (i,j,k).  Values are defined only where the
  * step computes them (see the regions in the library documentation). */
@@ -165,7 +166,7 @@ int hydro_kernel_launches(hydro_handle* h, int64_t* count);
  * record per stage (up to max_stages, in launch order; *nstages receives the
  * number of stages): kernels launched and summed device milliseconds. */
 typedef struct hydro_stage_time {
-  char name[24];    /* fill_ghosts, prim, dt, flatten, trace, riemann, ctu1, ctu2, update */
+  char name[24];    /* fill_ghosts, prim, dt, flatten, slopes, trace, riemann, ctu1, ctu2, update */
   int64_t launches; /* kernels launched in the stage while profiling */
   double total_ms;  /* summed event time of those launches */
 } hydro_stage_time;
@@ -179,7 +180,7 @@ int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, in
  * allocation, or a latency-critical loop that cannot pay for cudaMalloc /
  * cudaFree (which may stall or synchronise the device).  hydro_compute_dt
  * needs a handle, and a handle needs a caller-allocated scratch buffer of
- * about 97 doubles per ghosted zone; this call needs neither.
+ * about 112 doubles per ghosted zone; this call needs neither.
  *
  * Writes dt_dev[b] = cfl * min over interior zones and axes of dx/(|u|+c)
  * for boxes d[0..nboxes-1] whose states sit in state_dev with the layout

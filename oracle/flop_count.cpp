@@ -60,9 +60,11 @@ void put(long long* out, const OpCounts& c) {
 extern "C" {
 
 /* Runs one oracle step (ghosts of U already filled) with the given dt and
- * writes, per stage (prim, dt, flatten, trace, riemann, ctu1, ctu2, update),
- * out[stage*6 + (add, mul, div, sqrt, cmp, minmax)] and units[stage]: zones,
- * zone-directions or faces the stage processed. */
+ * writes, per stage (prim, dt, flatten, trace, riemann, ctu1, ctu2, update,
+ * slopes), out[stage*6 + (add, mul, div, sqrt, cmp, minmax)] and units[stage]:
+ * zones, zone-directions or faces the stage processed.  "trace" is the
+ * interface values plus the zone parabolas and tracing; "slopes" the limited
+ * slopes (per zone and axis of the slope region, five variables). */
 int oracle_count_step(int nx, int ny, int nz, const double* dx, double gamma, double cfl, const int* bc,
                       const double* U_in, double dt_in, long long* out, long long* units) {
   ob_box b;
@@ -85,8 +87,26 @@ int oracle_count_step(int nx, int ny, int nz, const double* dx, double gamma, do
   OpCounts s2 = g_ops;
   flatten_all(G, W + (long)W_Q * G.size, W + (long)W_CHI * G.size);
   OpCounts s3 = g_ops;
-  trace_all(&b, G, dt, W);
+  /* trace_all, with the slopes counted apart from interfaces + zone tracing */
+  cd* slope = (cd*)calloc((size_t)5 * G.size, sizeof(cd));
+  cd* face = (cd*)calloc((size_t)5 * G.size, sizeof(cd));
+  OpCounts sl = {0, 0, 0, 0, 0, 0};
+  for (int d = 0; d < 3; d++) {
+    OpCounts a = g_ops;
+    limited_slopes_dir(G, d, W, slope);
+    OpCounts bb = g_ops;
+    OpCounts dd = diff(bb, a);
+    sl.add += dd.add; sl.mul += dd.mul; sl.div += dd.div; sl.sqrt += dd.sqrt; sl.cmp += dd.cmp;
+    sl.minmax += dd.minmax;
+    interface_values_dir(G, d, W, slope, face);
+    trace_zones_dir(&b, G, d, dt, W, face);
+  }
+  free(slope);
+  free(face);
   OpCounts s4 = g_ops;
+  OpCounts tr = diff(s4, s3); /* interface values + zone tracing: trace_all minus the slopes */
+  tr.add -= sl.add; tr.mul -= sl.mul; tr.div -= sl.div; tr.sqrt -= sl.sqrt; tr.cmp -= sl.cmp;
+  tr.minmax -= sl.minmax;
   normal_fluxes(&b, G, W);
   OpCounts s5 = g_ops;
   ctu_stage1(&b, G, dt, W);
@@ -98,11 +118,12 @@ int oracle_count_step(int nx, int ny, int nz, const double* dx, double gamma, do
   put(out + 0, diff(s1, s0));
   put(out + 6, diff(s2, s1));
   put(out + 12, diff(s3, s2));
-  put(out + 18, diff(s4, s3));
+  put(out + 18, tr);
   put(out + 24, diff(s5, s4));
   put(out + 30, diff(s6, s5));
   put(out + 36, diff(s7, s6));
   put(out + 42, diff(s8, s7));
+  put(out + 48, sl);
   long long ext = (long long)(nx + 2) * (ny + 2) * (nz + 2);
   long long interior = (long long)nx * ny * nz;
   units[0] = G.size;
@@ -119,6 +140,8 @@ int oracle_count_step(int nx, int ny, int nz, const double* dx, double gamma, do
     units[6] += (long long)(n[d] + 1) * n[e] * n[f];
   }
   units[7] = interior;
+  units[8] = 0;
+  for (int d = 0; d < 3; d++) units[8] += (long long)(n[d] + 4) * (n[(d + 1) % 3] + 2) * (n[(d + 2) % 3] + 2);
   free(U);
   free(W);
   return ok ? 0 : -3;

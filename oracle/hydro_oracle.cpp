@@ -441,54 +441,73 @@ static void load_state(const double* W, long N, int base, int d, long Z, double*
 }
 
 /* ------------------------------------------------------------- one step */
-/* a4 + a5 for every direction: limited slopes of the five normal-frame
- * variables on zones [-2, n_d+1] along d, interface values on the faces
- * [-1, n_d+1] (each computed once and stored, the CPU structure the paper's
- * §3 describes), then per zone of [-1, n]^3 the limited parabolas and the
- * traced edge states. */
+/* a4: limited slopes of the five normal-frame variables of axis d on zones
+ * [-2, n_d+1] along d and [-1, n] across it (stored per zone: the CPU
+ * structure the paper's §3 describes) */
+static void limited_slopes_dir(const Grid& G, int d, const double* W, double* slope) {
+  long N = G.size, s = G.s[d];
+  const double* qn[5];
+  for (int m = 0; m < 5; m++) qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+  int lo[3] = {-1, -1, -1}, hi[3] = {G.n[0], G.n[1], G.n[2]};
+  lo[d] = -2;
+  hi[d] = G.n[d] + 1;
+#pragma omp parallel for schedule(static)
+  for (int k = lo[2]; k <= hi[2]; k++)
+    for (int j = lo[1]; j <= hi[1]; j++)
+      for (int i = lo[0]; i <= hi[0]; i++) {
+        long Z = G.at(i, j, k);
+        for (int m = 0; m < 5; m++) slope[(long)m * N + Z] = limited_slope(qn[m][Z - s], qn[m][Z], qn[m][Z + s]);
+      }
+}
+
+/* a4: interface values on the faces [-1, n_d+1] of axis d (one per face) */
+static void interface_values_dir(const Grid& G, int d, const double* W, const double* slope, double* face) {
+  long N = G.size, s = G.s[d];
+  const double* qn[5];
+  for (int m = 0; m < 5; m++) qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+  int lo[3] = {-1, -1, -1}, hi[3] = {G.n[0], G.n[1], G.n[2]};
+  hi[d] = G.n[d] + 1;
+#pragma omp parallel for schedule(static)
+  for (int k = lo[2]; k <= hi[2]; k++)
+    for (int j = lo[1]; j <= hi[1]; j++)
+      for (int i = lo[0]; i <= hi[0]; i++) {
+        long Z = G.at(i, j, k);
+        for (int m = 0; m < 5; m++) face[(long)m * N + Z] = interface_value(qn[m], slope + (long)m * N, Z, s);
+      }
+}
+
+/* a4 + a5: per zone of [-1, n]^3 the limited parabolas of axis d and the
+ * traced edge states */
+static void trace_zones_dir(const ob_box* b, const Grid& G, int d, double dt, double* W, const double* face) {
+  long N = G.size, s = G.s[d];
+  double dtdx = dt / b->dx[d];
+  const double* qn[5];
+  const double* fc[5];
+  for (int m = 0; m < 5; m++) {
+    qn[m] = W + (long)(W_Q + comp(d, m)) * N;
+    fc[m] = face + (long)m * N;
+  }
+#pragma omp parallel for schedule(static)
+  for (int k = -1; k <= G.n[2]; k++)
+    for (int j = -1; j <= G.n[1]; j++)
+      for (int i = -1; i <= G.n[0]; i++) {
+        long Z = G.at(i, j, k);
+        double qm[5], qp[5];
+        trace_zone(qn, fc, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, s, dtdx, qm, qp);
+        for (int m = 0; m < 5; m++) {
+          W[(long)(W_QM + 5 * d + m) * N + Z] = qm[m];
+          W[(long)(W_QP + 5 * d + m) * N + Z] = qp[m];
+        }
+      }
+}
+
 static void trace_all(const ob_box* b, const Grid& G, double dt, double* W) {
-  long N = G.size;
-  double* slope = (double*)calloc((size_t)5 * N, sizeof(double));
-  double* face = (double*)calloc((size_t)5 * N, sizeof(double));
+  double* slope = (double*)calloc((size_t)5 * G.size, sizeof(double));
+  double* face = (double*)calloc((size_t)5 * G.size, sizeof(double));
   for (int d = 0; d < 3; d++) {
-    double dtdx = dt / b->dx[d];
-    long s = G.s[d];
-    const double* qn[5];
-    const double* fc[5];
-    for (int m = 0; m < 5; m++) {
-      qn[m] = W + (long)(W_Q + comp(d, m)) * N;
-      fc[m] = face + (long)m * N;
-    }
-    int lo[3] = {-1, -1, -1}, hi[3] = {G.n[0], G.n[1], G.n[2]};
-    lo[d] = -2;
-    hi[d] = G.n[d] + 1;
-#pragma omp parallel for schedule(static)
-    for (int k = lo[2]; k <= hi[2]; k++)
-      for (int j = lo[1]; j <= hi[1]; j++)
-        for (int i = lo[0]; i <= hi[0]; i++) {
-          long Z = G.at(i, j, k);
-          for (int m = 0; m < 5; m++) slope[(long)m * N + Z] = limited_slope(qn[m][Z - s], qn[m][Z], qn[m][Z + s]);
-        }
-    lo[d] = -1;
-#pragma omp parallel for schedule(static)
-    for (int k = lo[2]; k <= hi[2]; k++)
-      for (int j = lo[1]; j <= hi[1]; j++)
-        for (int i = lo[0]; i <= hi[0]; i++) {
-          long Z = G.at(i, j, k);
-          for (int m = 0; m < 5; m++) face[(long)m * N + Z] = interface_value(qn[m], slope + (long)m * N, Z, s);
-        }
-#pragma omp parallel for schedule(static)
-    for (int k = -1; k <= G.n[2]; k++)
-      for (int j = -1; j <= G.n[1]; j++)
-        for (int i = -1; i <= G.n[0]; i++) {
-          long Z = G.at(i, j, k);
-          double qm[5], qp[5];
-          trace_zone(qn, fc, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, s, dtdx, qm, qp);
-          for (int m = 0; m < 5; m++) {
-            W[(long)(W_QM + 5 * d + m) * N + Z] = qm[m];
-            W[(long)(W_QP + 5 * d + m) * N + Z] = qp[m];
-          }
-        }
+    limited_slopes_dir(G, d, W, slope);
+    interface_values_dir(G, d, W, slope, face);
+    trace_zones_dir(b, G, d, dt, W, face);
   }
   free(slope);
   free(face);

@@ -13,6 +13,7 @@
 //   k_prim       conserved -> primitive + EOS; per-box max signal speed for dt
 //   k_dt         dt = cfl / max((|u_d|+c)/dx_d)
 //   k_flatten    CW84 §4 shock flattening coefficient (max over directions)
+//   k_slopes     CW84 limited slopes, once per zone and axis
 //   k_trace      CW84 PPM parabolas + characteristic tracing -> face states
 //   k_riemann    HLLC normal fluxes F0_d on the extended face region
 //   k_ctu1       3D CTU stage 1: dt/(3dx_e) transverse corrections + HLLC
@@ -21,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "fp64_fast.cuh"
 #include "hydro_internal.cuh"
 
 namespace hydro {
@@ -101,11 +103,11 @@ __global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, 
     double* W = work + b.work_off;
     double rho = U[Z];
     if (rho < SMALL_DENS) rho = SMALL_DENS;
-    const double ir = 1.0 / rho;
+    const double ir = nr_rcp(rho);
     const double u = U[vs + Z] * ir, v = U[2 * vs + Z] * ir, w = U[3 * vs + Z] * ir;
     double p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
     if (p < SMALL_PRES) p = SMALL_PRES;
-    const double cs = sqrt(b.gamma * p * ir);
+    const double cs = nr_sqrt(b.gamma * p * ir);
     W[Z] = rho;
     W[vs + Z] = u;
     W[2 * vs + Z] = v;
@@ -171,49 +173,80 @@ __global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxe
 }
 
 // ------------------------------------------------------------- PPM + tracing
+// van Leer limited slope at a0 (CW84 eq. 1.8); the sign test and the minimum
+// run on the integer pipe (magnitudes order like their bit patterns).
 __device__ __forceinline__ double vl_slope(double am, double a0, double ap) {
   const double dl = a0 - am, dr = ap - a0;
-  if (dl * dr > 0.0) {
-    const double dc = 0.5 * (ap - am);
-    return copysign(fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr))), dc);
-  }
-  return 0.0;
+  if (!same_sign(dl, dr)) return 0.0;
+  const double dc = 0.5 * (ap - am);
+  long long m = dbits(fabs(dc));
+  m = min(m, dbits(2.0 * fabs(dl)));
+  m = min(m, dbits(2.0 * fabs(dr)));
+  return copysign(__longlong_as_double(m), dc);
 }
 
-// CW84 eqs. 1.6-1.10 on the five-zone stencil a[0..4] (zone i = a[2]), then flattening
-__device__ __forceinline__ void parabola(const double* a, double f, double& L, double& R) {
-  const double dm1 = vl_slope(a[0], a[1], a[2]);
-  const double d0 = vl_slope(a[1], a[2], a[3]);
-  const double dp1 = vl_slope(a[2], a[3], a[4]);
-  const double a0 = a[2];
-  L = a[1] + 0.5 * (a0 - a[1]) - (d0 - dm1) * (1.0 / 6.0);
-  R = a0 + 0.5 * (a[3] - a0) - (dp1 - d0) * (1.0 / 6.0);
-  if ((R - a0) * (a0 - L) <= 0.0) {
+// Limited slopes of the five normal-frame variables of axis D, once per zone
+// of [-2, n_D+1] along D and [-1, n] across it.
+template <int D>
+__device__ __forceinline__ void slopes_zone(const DevBox& b, double* __restrict__ W, long long Z) {
+  const long long vs = b.vs, s = b.s[D];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    const double* a = W + comp<D>(m) * vs + Z;
+    W[(FLD_DQ + 5 * D + m) * vs + Z] = vl_slope(a[-s], a[0], a[s]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_slopes(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+  const DevBox& b = boxes[blockIdx.y];
+  const int d = blockIdx.z;
+  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
+  lo[d] = -2;
+  ext[d] = b.n[d] + 4;
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* W = work + b.work_off;
+  switch (d) {
+    case 0: slopes_zone<0>(b, W, Z); break;
+    case 1: slopes_zone<1>(b, W, Z); break;
+    default: slopes_zone<2>(b, W, Z); break;
+  }
+}
+
+// Parabola of zone value a0 with neighbours am1, ap1 and limited slopes
+// dm1, d0, dp1: interface values (CW84 eq. 1.6), monotonicity limiter
+// (eq. 1.10) with its tests on the integer pipe, then flattening by f.
+__device__ __forceinline__ void parabola(double am1, double a0, double ap1, double dm1, double d0, double dp1,
+                                         double f, double& L, double& R) {
+  L = am1 + 0.5 * (a0 - am1) - (d0 - dm1) * (1.0 / 6.0);
+  R = a0 + 0.5 * (ap1 - a0) - (dp1 - d0) * (1.0 / 6.0);
+  if (!same_sign(R - a0, a0 - L)) {
     L = a0;
     R = a0;
   } else {
     const double dA = R - L;
     const double t1 = dA * (a0 - 0.5 * (L + R));
     const double t2 = dA * dA * (1.0 / 6.0);
-    if (t1 > t2) L = 3.0 * a0 - 2.0 * R;
-    else if (-t2 > t1) R = 3.0 * a0 - 2.0 * L;
+    if (dgt(t1, t2)) L = 3.0 * a0 - 2.0 * R;
+    else if (dgt(-t2, t1)) R = 3.0 * a0 - 2.0 * L;
   }
-  L = f * a0 + (1.0 - f) * L;
-  R = f * a0 + (1.0 - f) * R;
+  if (is_pos(f)) {
+    L = f * a0 + (1.0 - f) * L;
+    R = f * a0 + (1.0 - f) * R;
+  }
 }
 
 template <int D>
 __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__ W, long long Z, double dtdx) {
   const long long vs = b.vs, s = b.s[D];
+  const double f = W[FLD_CHI * vs + Z];
   double a0[5], aL[5], aR[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
-    const double* src = W + comp<D>(m) * vs + Z;
-    double a[5];
-#pragma unroll
-    for (int o = 0; o < 5; o++) a[o] = src[(o - 2) * s];
-    a0[m] = a[2];
-    parabola(a, W[FLD_CHI * vs + Z], aL[m], aR[m]);
+    const double* a = W + comp<D>(m) * vs + Z;
+    const double* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
+    a0[m] = a[0];
+    parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
   }
   double dA[5], a6[5];
 #pragma unroll
@@ -223,17 +256,17 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
   }
   const double cs = W[FLD_C * vs + Z];
   const double rho = a0[0], u = a0[1];
-  const double ic = 1.0 / cs;
+  const double ic = nr_rcp(cs);
   const double rc = 0.5 * rho * ic;   // rho / 2c
   const double i2c2 = 0.5 * ic * ic;  // 1 / 2c^2
   const double ic2 = ic * ic;         // 1 / c^2
-  const double cr = cs / rho;         // c / rho
+  const double cr = cs * nr_rcp(rho); // c / rho
   const double c2 = cs * cs;
   const double lm = u - cs, lp = u + cs;
 
   double out[5];
   // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
-  if (lp > 0.0) {
+  if (is_pos(lp)) {
     double sg = lp * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
     double ref[5];
 #pragma unroll
@@ -241,13 +274,13 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
     double bm = 0.0, b0 = 0.0;
     out[2] = ref[2];
     out[3] = ref[3];
-    if (lm > 0.0) {
+    if (is_pos(lm)) {
       sg = lm * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
       const double du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * a6[1]));
       const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
       bm = -rc * du + i2c2 * dp;
     }
-    if (u > 0.0) {
+    if (is_pos(u)) {
       sg = u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
       const double dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * a6[0]));
       const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
@@ -262,13 +295,13 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
 #pragma unroll
     for (int m = 0; m < 5; m++) out[m] = a0[m];
   }
-  if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
-  if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+  if (dgt(SMALL_DENS, out[0])) out[0] = SMALL_DENS;
+  if (dgt(SMALL_PRES, out[4])) out[4] = SMALL_PRES;
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
-  if (lm < 0.0) {
+  if (is_neg(lm)) {
     double sg = -lm * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
     double ref[5];
 #pragma unroll
@@ -276,13 +309,13 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
     double bp = 0.0, b0 = 0.0;
     out[2] = ref[2];
     out[3] = ref[3];
-    if (lp < 0.0) {
+    if (is_neg(lp)) {
       sg = -lp * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
       const double du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * a6[1]));
       const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
       bp = rc * du + i2c2 * dp;
     }
-    if (u < 0.0) {
+    if (is_neg(u)) {
       sg = -u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
       const double dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * a6[0]));
       const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
@@ -297,8 +330,8 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
 #pragma unroll
     for (int m = 0; m < 5; m++) out[m] = a0[m];
   }
-  if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
-  if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+  if (dgt(SMALL_DENS, out[0])) out[0] = SMALL_DENS;
+  if (dgt(SMALL_PRES, out[4])) out[4] = SMALL_PRES;
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
 }
@@ -322,17 +355,23 @@ __global__ void __launch_bounds__(TPB) k_trace(const DevBox* __restrict__ boxes,
 // Normal-frame states (rho, u_n, u_t1, u_t2, p) -> normal-frame flux.
 // Toro, Spruce & Speares 1994 with Roe-averaged bounds (Batten et al. 1997),
 // Davis bounds when the Roe sound speed is not real.  Only the star state on
-// the side of the contact that contains x/t = 0 is formed.
+// the side of the contact that contains x/t = 0 is formed.  All square roots
+// and reciprocals come from two reciprocal square roots per side (sqrt(rho),
+// 1/rho, c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed)
+// and three reciprocals; wave-speed min/max and sign tests run on the integer
+// pipe.
 __device__ __forceinline__ void hllc(const double* L, const double* R, double gamma, double igm1, double* F) {
   const double gm1 = gamma - 1.0;
   const double rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
   const double rr = R[0], ur = R[1], vr = R[2], wr = R[3], pr = R[4];
-  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  const double rsl = nr_rsqrt(rl), rsr = nr_rsqrt(rr);  // 1/sqrt(rho)
+  const double sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
+  const double irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
+  const double gpl = gamma * pl, gpr = gamma * pr;
+  const double cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
   const double El = pl * igm1 + 0.5 * rl * (ul * ul + vl * vl + wl * wl);
   const double Er = pr * igm1 + 0.5 * rr * (ur * ur + vr * vr + wr * wr);
-  const double cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
-  const double sl = sqrt(rl), sr = sqrt(rr);
-  const double iw = 1.0 / (sl + sr);
+  const double iw = nr_rcp(sl + sr);
   const double wgl = sl * iw, wgr = sr * iw;
   const double ut = wgl * ul + wgr * ur;
   const double vt = wgl * vl + wgr * vr;
@@ -340,17 +379,17 @@ __device__ __forceinline__ void hllc(const double* L, const double* R, double ga
   const double Ht = wgl * ((El + pl) * irl) + wgr * ((Er + pr) * irr);
   const double ct2 = gm1 * (Ht - 0.5 * (ut * ut + vt * vt + wt * wt));
   double SL, SR;
-  if (ct2 > 0.0) {
-    const double ct = sqrt(ct2);
-    SL = fmin(ul - cl, ut - ct);
-    SR = fmax(ur + cr, ut + ct);
+  if (is_pos(ct2)) {
+    const double ct = nr_sqrt(ct2);
+    SL = dmin(ul - cl, ut - ct);
+    SR = dmax(ur + cr, ut + ct);
   } else {
-    SL = fmin(ul - cl, ur - cr);
-    SR = fmax(ul + cl, ur + cr);
+    SL = dmin(ul - cl, ur - cr);
+    SR = dmax(ul + cl, ur + cr);
   }
   const double ml = rl * (SL - ul), mr = rr * (SR - ur);
-  const double Ss = (pr - pl + ml * ul - mr * ur) / (ml - mr);
-  const bool left = Ss >= 0.0;
+  const double Ss = (pr - pl + ml * ul - mr * ur) * nr_rcp(ml - mr);
+  const bool left = is_nonneg(Ss);
   const double rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
   const double pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
   const double irK = left ? irl : irr;
@@ -360,10 +399,13 @@ __device__ __forceinline__ void hllc(const double* L, const double* R, double ga
   F[2] = mu * vK;
   F[3] = mu * wK;
   F[4] = (EK + pK) * uK;
-  const bool supersonic = left ? (SL >= 0.0) : (SR <= 0.0);
+  const bool supersonic = left ? is_nonneg(SL) : !is_pos(SR);
   if (!supersonic) {
-    const double fac = mK / (SK - Ss);
-    const double eK = EK * irK + (Ss - uK) * (Ss + pK / mK);
+    // fac = mK / (SK - S*) and pK / mK from one reciprocal of mK (SK - S*)
+    const double den = SK - Ss;
+    const double r = nr_rcp(mK * den);
+    const double fac = mK * mK * r;
+    const double eK = EK * irK + (Ss - uK) * (Ss + pK * den * r);
     F[0] += SK * (fac - rK);
     F[1] += SK * (fac * Ss - mu);
     F[2] += SK * (fac * vK - rK * vK);
@@ -431,16 +473,16 @@ __device__ __forceinline__ void correct(double* q, const double* const* Fb, cons
 #pragma unroll
     for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * (Fb[t][off + st[t]] - Fb[t][off]);
   }
-  if (U[0] > 0.0) {
-    const double ir = 1.0 / U[0];
+  if (is_pos(U[0])) {
+    const double ir = nr_rcp(U[0]);
     const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
     const double p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w));
-    if (p > 0.0) {
+    if (is_pos(p)) {
       q[0] = U[0];
       q[1] = u;
       q[2] = v;
       q[3] = w;
-      q[4] = p < SMALL_PRES ? SMALL_PRES : p;
+      q[4] = dgt(SMALL_PRES, p) ? SMALL_PRES : p;
     }
   }
 }
@@ -612,9 +654,9 @@ dim3 grid_for(long long vol, int tpb, int nboxes, int z = 1) {
 
 }  // namespace
 
-const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "trace",
+const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "slopes", "trace",
                                            "riemann", "ctu1", "ctu2", "update"};
-const int STAGE_KERNELS[NSTAGES] = {3, 1, 1, 1, 1, 1, 1, 1, 1};
+const int STAGE_KERNELS[NSTAGES] = {3, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
                          int advance) {
@@ -642,6 +684,18 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
     case ST_FLATTEN:
       k_flatten<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes), TPB, 0, stream>>>(p.dboxes, p.work);
       break;
+    case ST_SLOPES: {
+      // slope region: axis d has n+4 zones, the transverse axes n+2
+      long long vs0 = 0;
+      for (int i = 0; i < p.nboxes; i++) {
+        const hydro_box_desc& d = p.boxes[i].d;
+        const int n[3] = {d.nx, d.ny, d.nz};
+        for (int a = 0; a < 3; a++)
+          vs0 = std::max(vs0, (long long)(n[a] + 4) * (n[(a + 1) % 3] + 2) * (n[(a + 2) % 3] + 2));
+      }
+      k_slopes<<<grid_for(vs0, 256, p.nboxes, 3), 256, 0, stream>>>(p.dboxes, p.work);
+      break;
+    }
     case ST_TRACE:
       k_trace<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
       break;

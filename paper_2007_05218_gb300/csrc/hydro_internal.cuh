@@ -25,7 +25,8 @@ constexpr double FLAT_OMEGA2 = 10.0;
 //   qm[d][5] / qp[d][5] traced left-/right-edge states in the normal frame of d
 //   (rho, u_n, u_t1, u_t2, p with t1 = (d+1)%3, t2 = (d+2)%3),
 //   f0[d][5] normal fluxes, f1[pair][5] singly corrected fluxes for the ordered
-//   pairs (d,e) = xy,xz,yx,yz,zx,zy, f[d][5] final fluxes (conserved x,y,z order).
+//   pairs (d,e) = xy,xz,yx,yz,zx,zy, f[d][5] final fluxes (conserved x,y,z order),
+//   dq[d][5] limited slopes of the normal-frame variables of axis d.
 // Flux of a d-face between zones Z-s_d and Z is stored at zone Z.
 enum Field : int {
   FLD_Q = 0,
@@ -36,7 +37,8 @@ enum Field : int {
   FLD_F0 = 37,
   FLD_F1 = 52,
   FLD_F = 82,
-  NFIELDS = 97
+  FLD_DQ = 97,
+  NFIELDS = 112
 };
 
 // Per-box geometry as the kernels see it (lives in the head of scratch).
@@ -96,6 +98,7 @@ enum Stage : int {
   ST_PRIM,
   ST_DT,
   ST_FLATTEN,
+  ST_SLOPES,
   ST_TRACE,
   ST_RIEMANN,
   ST_CTU1,

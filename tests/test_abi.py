@@ -48,7 +48,7 @@ def test_workspace_and_layout_planning():
     assert lay.var_stride >= lay.plane * 17 and lay.var_stride % 32 == 0
     assert sb == 5 * lay.var_stride * 8
     off, nf = hydro.hydro_debug_fields([d], 0)
-    assert nf == 97
+    assert nf == 112
     assert wb >= (off + nf * lay.var_stride) * 8
     # two boxes: the second starts right after the first
     d2 = hydro.desc_of(inputs.sod((32, 4, 4)))
