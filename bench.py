@@ -277,6 +277,37 @@ def main() -> None:
            "what": "hydro_upload of the interior initial state from pinned host memory, K steps, "
                    "hydro_download of the final interior state (bytes per step = solve bytes / K)"}
     B.close()
+    del B
+    fp64_final = host_out.numpy().reshape(pr.U.shape)
+
+    # ---- mixed precision on the same workload: W warm-up steps, re-upload the
+    # initial state, K timed steps; accuracy against the FP64 result after the
+    # same K steps from the same initial state
+    M = hydro.Boxes([pr], precision=hydro.HYDRO_MIXED)
+    M.step(args.warmup)
+    M.sync()
+    hydro.hydro_upload(M.h, host_in.numpy(), stream)
+    hydro.hydro_get_time(M.h, 1, stream)
+    barrier()
+    torch.cuda.synchronize()
+    hydro.hydro_profile_begin(M.h)
+    e0.record(stream)
+    for _ in range(args.steps):
+        hydro.hydro_step(M.h, None, 1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mixed = e0.elapsed_time(e1)
+    prof_mixed = hydro.hydro_profile_end(M.h)
+    M.sync()
+    mixed_final = np.zeros_like(fp64_final)
+    hydro.hydro_download(M.h, mixed_final, stream)
+    M.close()
+    del M
+    rel_l1 = {name: float(np.abs(mixed_final[v] - fp64_final[v]).sum() / np.abs(fp64_final[v]).sum())
+              for name, v in (("rho", 0), ("E", 4))}
+    mixed = {"value": world * N * args.steps / (ms_mixed * 1e-3), "unit": UNIT,
+             "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
+             "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
 
     if rank != 0:
         if dist is not None:
@@ -319,6 +350,7 @@ def main() -> None:
         "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "mixed": mixed,
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -59,7 +59,10 @@ extern "C" {
 
 /* ---- precision of the reconstruction/Riemann stages ---- */
 #define HYDRO_FP64 0  /* every stage in FP64 */
-#define HYDRO_MIXED 1 /* reserved: FP32 reconstruction/tracing/Riemann, FP64 update and dt */
+#define HYDRO_MIXED 1 /* FP32 flattening, reconstruction, tracing, CTU corrections and Riemann
+                         solves (FP32 scratch fields); FP64 state, primitive conversion, dt
+                         reduction and flux-divergence update, so each face flux is applied to
+                         both neighbours in FP64 and conservation holds to FP64 round-off */
 
 #define HYDRO_NG 4 /* ghost zones per side (the only supported value) */
 
@@ -71,7 +74,7 @@ typedef struct hydro_box_desc {
   double gamma;       /* ratio of specific heats, > 1 */
   double cfl;         /* Courant number, in (0, 1] */
   int32_t bc[6];      /* HYDRO_BC_* for faces xlo, xhi, ylo, yhi, zlo, zhi */
-  int32_t precision;  /* HYDRO_FP64 */
+  int32_t precision;  /* HYDRO_FP64 or HYDRO_MIXED; boxes of one handle may differ */
 } hydro_box_desc;
 
 /* Where box `box` lives inside the state buffer, in FP64 elements.
@@ -141,20 +144,22 @@ int hydro_upload(hydro_handle* h, const double* state_host, size_t bytes, void* 
 int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stream);
 
 /* Diagnostics: where the per-zone intermediates of box `box` live inside the
- * scratch buffer, for stage-by-stage checks.  *offset receives the element
- * (FP64) offset of the box's first field from the start of scratch_dev and
- * *nfields the number of fields (112).  Each field is a ghosted-box grid with
- * the state's pitch, plane and var_stride (fields are var_stride apart), in
- * this order: primitive q[5] = (rho,u,v,w,p); sound speed c; flattening
- * coefficient chi; left-edge states qm[3][5] and right-edge states qp[3][5]
- * per axis d in the normal frame of d (rho, u_d, u_{d+1}, u_{d+2}, p, axis
- * indices mod 3); normal fluxes f0[3][5]; once-corrected fluxes f1[6][5] for
- * the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes f[3][5]; limited
- * slopes dq[3][5] of the normal-frame variables of each axis.  Fluxes are
- * conserved-variable components; the flux through the low face of zone
- * (i,j,k) along d is stored at (i,j,k).  Values are defined only where the
- * step computes them (see the regions in the library documentation). */
-int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset, int32_t* nfields);
+ * scratch buffer, for stage-by-stage checks.  *offset_bytes receives the byte
+ * offset of the box's first field from the start of scratch_dev, *nfields the
+ * number of fields (112) and *elem_bytes their element size (8 for
+ * HYDRO_FP64, 4 for HYDRO_MIXED boxes).  Each field is a ghosted-box grid with
+ * the state's pitch, plane and var_stride (in elements; fields are var_stride
+ * elements apart), in this order: primitive q[5] = (rho,u,v,w,p); sound speed
+ * c; flattening coefficient chi; left-edge states qm[3][5] and right-edge
+ * states qp[3][5] per axis d in the normal frame of d (rho, u_d, u_{d+1},
+ * u_{d+2}, p, axis indices mod 3); normal fluxes f0[3][5]; once-corrected
+ * fluxes f1[6][5] for the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes
+ * f[3][5]; limited slopes dq[3][5] of the normal-frame variables of each axis.
+ * Fluxes are conserved-variable components; the flux through the low face of
+ * zone (i,j,k) along d is stored at (i,j,k).  Values are defined only where
+ * the step computes them. */
+int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset_bytes, int32_t* nfields,
+                       int32_t* elem_bytes);
 
 /* Number of kernels this handle has launched since hydro_alloc (a ghost fill
  * is three kernels, every other stage one), into *count. */

@@ -38,6 +38,9 @@
  *       computed from the state before the step.
  *   R8  ghost fill in the order x, y, z (later directions span the earlier
  *       directions' ghosts, so edges and corners are filled).
+ *   R11 the final flux through a reflecting face carries no mass, energy or
+ *       tangential momentum (the wall is impermeable; only the normal
+ *       momentum flux, the wall pressure, is kept).
  *
  * Layout: every field is a [k][j][i] array over the ghosted box
  * (nx+2g)(ny+2g)(nz+2g), i fastest, no padding.  Conserved state
@@ -608,6 +611,13 @@ static void ctu_stage2(const ob_box* b, const Grid& G, double dt, double* W) {
           corrected_state(b, qL0, 2, fac, Fs, s, ZL, N, qL);
           corrected_state(b, qR0, 2, fac, Fs, s, Z, N, qR);
           hllc_xyz(d, qL, qR, b->gamma, F);
+          /* R11: a reflecting face is impermeable -- no mass, energy or
+           * tangential momentum crosses it, only the pressure force acts */
+          int face = d == 0 ? i : (d == 1 ? j : k);
+          if ((face == 0 && b->bc[2 * d] == OB_REFLECT) || (face == G.n[d] && b->bc[2 * d + 1] == OB_REFLECT)) {
+            for (int v = 0; v < 5; v++)
+              if (v != 1 + d) F[v] = 0.0;
+          }
           for (int v = 0; v < 5; v++) out[v * N + Z] = F[v];
         }
   }

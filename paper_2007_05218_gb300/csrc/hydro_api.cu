@@ -23,6 +23,7 @@ struct hydro_handle {
   bool profiling = false;            // record an event pair around every stage launch
   std::vector<cudaEvent_t> events;   // event pool (pairs), reused across sessions
   std::vector<int> rec_stage;        // stage of each recorded pair
+  std::vector<int> rec_kernels;      // kernels launched inside each recorded pair
 };
 
 namespace {
@@ -60,7 +61,7 @@ int validate(const hydro_box_desc& d, int i) {
       return bad("unknown boundary condition");
     if ((lo == HYDRO_BC_PERIODIC) != (hi == HYDRO_BC_PERIODIC)) return bad("periodic faces must pair");
   }
-  if (d.precision != HYDRO_FP64) return bad("precision must be HYDRO_FP64");
+  if (d.precision != HYDRO_FP64 && d.precision != HYDRO_MIXED) return bad("precision must be HYDRO_FP64 or HYDRO_MIXED");
   return HYDRO_OK;
 }
 
@@ -68,7 +69,7 @@ struct Geometry {
   std::vector<HostBox> boxes;
   size_t state_elems = 0;
   size_t table_bytes = 0, rt_bytes = 0, head_bytes = 0;
-  size_t work_elems = 0, stage_elems = 0;
+  size_t work_bytes = 0, stage_elems = 0;
   size_t scratch_bytes = 0;
 };
 
@@ -90,16 +91,18 @@ int plan_geometry(const hydro_box_desc* d, int nboxes, Geometry* g) {
     hb.work_off = woff;
     hb.stage_off = stoff;
     soff += 5 * hb.vs;
-    woff += (long long)hydro::NFIELDS * hb.vs;
+    const size_t elem = d[i].precision == HYDRO_MIXED ? sizeof(float) : sizeof(double);
+    woff += (long long)align_up((size_t)hydro::NFIELDS * hb.vs * elem, ALIGN);
     stoff += 5 * hb.interior;
   }
   g->state_elems = (size_t)soff;
-  g->work_elems = (size_t)woff;
+  g->work_bytes = (size_t)woff;
   g->stage_elems = (size_t)stoff;
   g->table_bytes = align_up(sizeof(DevBox) * nboxes, ALIGN);
   g->rt_bytes = align_up(sizeof(BoxRt) * nboxes, ALIGN);
   g->head_bytes = g->table_bytes + g->rt_bytes;
-  g->scratch_bytes = g->head_bytes + g->work_elems * sizeof(double);
+  // the field area doubles as the staging buffer of hydro_upload/download
+  g->scratch_bytes = g->head_bytes + std::max(g->work_bytes, g->stage_elems * sizeof(double));
   return HYDRO_OK;
 }
 
@@ -130,12 +133,14 @@ cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const do
     cudaError_t err = cudaEventRecord(ev[0], s);
     if (err != cudaSuccess) return err;
   }
-  cudaError_t e = hydro::launch_stage(h->plan, st, s, dt_in, dt_out, advance);
+  int n = 0;
+  cudaError_t e = hydro::launch_stage(h->plan, st, s, dt_in, dt_out, advance, &n);
   if (e != cudaSuccess) return e;
-  h->launches += hydro::STAGE_KERNELS[st];
+  h->launches += n;
   if (h->profiling) {
     e = cudaEventRecord(ev[1], s);
     h->rec_stage.push_back((int)st);
+    h->rec_kernels.push_back(n);
   }
   return e;
 }
@@ -174,14 +179,16 @@ int hydro_box_layout(const hydro_box_desc* d, int nboxes, int box, hydro_layout*
   return HYDRO_OK;
 }
 
-int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset, int32_t* nfields) {
-  if (!offset || !nfields) return fail(HYDRO_ERR_INVALID, "null output pointer");
+int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset_bytes, int32_t* nfields,
+                       int32_t* elem_bytes) {
+  if (!offset_bytes || !nfields || !elem_bytes) return fail(HYDRO_ERR_INVALID, "null output pointer");
   Geometry g;
   int rc = plan_geometry(d, nboxes, &g);
   if (rc) return rc;
   if (box < 0 || box >= nboxes) return fail(HYDRO_ERR_INVALID, "box index out of range");
-  *offset = (int64_t)(g.head_bytes / sizeof(double)) + g.boxes[box].work_off;
+  *offset_bytes = (int64_t)g.head_bytes + g.boxes[box].work_off;
   *nfields = hydro::NFIELDS;
+  *elem_bytes = d[box].precision == HYDRO_MIXED ? (int32_t)sizeof(float) : (int32_t)sizeof(double);
   return HYDRO_OK;
 }
 
@@ -214,8 +221,10 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
   p.dboxes = reinterpret_cast<DevBox*>(scratch);
   p.rt = reinterpret_cast<BoxRt*>(scratch + g.table_bytes);
   p.state = static_cast<double*>(state_dev);
-  p.work = reinterpret_cast<double*>(scratch + g.head_bytes);
-  p.work_elems = g.work_elems;
+  p.work = reinterpret_cast<unsigned char*>(scratch + g.head_bytes);
+  p.work_bytes = g.work_bytes;
+  p.has_fp64 = false;
+  p.has_mixed = false;
   p.max_interior = 0;
   p.max_ghosted = 0;
   for (int a = 0; a < 3; a++) p.max_n[a] = 0;
@@ -247,6 +256,8 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
     db.cfl = hb.d.cfl;
     for (int f = 0; f < 6; f++) db.bc[f] = hb.d.bc[f];
     p.max_interior = std::max(p.max_interior, hb.interior);
+    if (hb.d.precision == HYDRO_MIXED) p.has_mixed = true;
+    else p.has_fp64 = true;
     p.max_ghosted = std::max(p.max_ghosted, hb.vs);
   }
   e = cudaMemcpy(p.dboxes, table.data(), sizeof(DevBox) * nboxes, cudaMemcpyHostToDevice);
@@ -350,8 +361,9 @@ int hydro_upload(hydro_handle* h, const double* state_host, size_t bytes, void* 
   for (const HostBox& hb : h->boxes) need += 5 * (size_t)hb.interior * sizeof(double);
   if (bytes != need) return fail(HYDRO_ERR_INVALID, "upload size does not match the boxes' interiors");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(h->plan.work, state_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = hydro::launch_scatter(h->plan, h->plan.work, s);
+  double* stage = reinterpret_cast<double*>(h->plan.work);
+  cudaError_t e = cudaMemcpyAsync(stage, state_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = hydro::launch_scatter(h->plan, stage, s);
   h->launches += 1;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return launched(e, "hydro_upload");
@@ -365,9 +377,10 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
   for (const HostBox& hb : h->boxes) need += 5 * (size_t)hb.interior * sizeof(double);
   if (bytes != need) return fail(HYDRO_ERR_INVALID, "download size does not match the boxes' interiors");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = hydro::launch_gather(h->plan, h->plan.work, s);
+  double* stage = reinterpret_cast<double*>(h->plan.work);
+  cudaError_t e = hydro::launch_gather(h->plan, stage, s);
   h->launches += 1;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(state_host, h->plan.work, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(state_host, stage, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return launched(e, "hydro_download");
 }
@@ -381,6 +394,7 @@ int hydro_kernel_launches(hydro_handle* h, int64_t* count) {
 int hydro_profile_begin(hydro_handle* h) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
   h->rec_stage.clear();
+  h->rec_kernels.clear();
   h->profiling = true;
   return HYDRO_OK;
 }
@@ -396,9 +410,10 @@ int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, in
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, h->events[2 * r], h->events[2 * r + 1]);
     if (e != cudaSuccess) return cuda_fail(e, "hydro_profile_end");
     ms[h->rec_stage[r]] += t;
-    n[h->rec_stage[r]] += hydro::STAGE_KERNELS[h->rec_stage[r]];
+    n[h->rec_stage[r]] += h->rec_kernels[r];
   }
   h->rec_stage.clear();
+  h->rec_kernels.clear();
   *nstages = hydro::NSTAGES;
   for (int s = 0; s < hydro::NSTAGES && s < max_stages; s++) {
     memset(&out[s], 0, sizeof out[s]);

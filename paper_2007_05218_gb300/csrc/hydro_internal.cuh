@@ -48,7 +48,7 @@ struct DevBox {
   long long s[3];         // element strides of i, j, k
   long long vs;           // element stride between fields/variables
   long long state_off;    // first state element of this box
-  long long work_off;     // first scratch element of this box's fields
+  long long work_off;     // byte offset of this box's fields in the field area
   long long stage_off;    // first element of this box in the compact host staging layout
   double dx[3];
   double idx[3];          // 1/dx
@@ -74,7 +74,7 @@ constexpr unsigned STATUS_NONPHYSICAL = 1u;
 struct HostBox {
   hydro_box_desc d;
   long long pitch, plane, vs;
-  long long state_off, work_off, stage_off;
+  long long state_off, work_off, stage_off;  // work_off in bytes
   long long interior;  // nx*ny*nz
 };
 
@@ -85,8 +85,9 @@ struct Plan {
   DevBox* dboxes;      // device table (in scratch)
   BoxRt* rt;           // device runtime records (in scratch)
   double* state;
-  double* work;        // start of the per-box field area (in scratch)
-  size_t work_elems;   // elements of the field area
+  unsigned char* work; // start of the per-box field area (in scratch)
+  size_t work_bytes;   // bytes of the field area
+  bool has_fp64, has_mixed;
   int max_n[3];        // max interior extent per axis over boxes
   long long max_ghosted, max_interior;
 };
@@ -107,14 +108,13 @@ enum Stage : int {
   NSTAGES
 };
 extern const char* const STAGE_NAMES[NSTAGES];
-extern const int STAGE_KERNELS[NSTAGES];
 
-// Launches one stage for every box of the plan (hydro_fp64.cu), asynchronously
-// on `stream`.  ST_DT uses dt_in[b] when dt_in is not null (else cfl/smax),
-// writes dt_out[b] when dt_out is not null, and advances the per-box time when
-// `advance` is set.
-cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in = nullptr,
-                         double* dt_out = nullptr, int advance = 0);
+// Launches one stage for every box of the plan (hydro_kernels.cu),
+// asynchronously on `stream`; *launched receives the number of kernels.
+// ST_DT uses dt_in[b] when dt_in is not null (else cfl/smax), writes dt_out[b]
+// when dt_out is not null, and advances the per-box time when `advance` is set.
+cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
+                         int advance, int* launched);
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream);
 // Sets the thread-local message returned by hydro_last_error (hydro_api.cu).
 void set_last_error(const std::string& msg);

@@ -1,16 +1,24 @@
-// FP64 kernels of the unsplit PPM/CTU/HLLC update, one kernel per stage with
+// Stage kernels of the unsplit PPM/CTU/HLLC update, one kernel per stage with
 // the intermediates in HBM scratch.
 //
-// Design for GB300: the update costs thousands of FP64 operations per zone
-// and GB300's FP64 pipe is narrow, while HBM bandwidth is plentiful.  So every
-// quantity is computed once and parked in HBM rather than recomputed by
-// neighbouring threads: the stage kernels read their stencil from scratch
+// Design for GB300: the update costs thousands of floating-point operations
+// per zone and GB300's FP64 pipe is narrow, while HBM bandwidth is plentiful.
+// So every quantity is computed once and parked in HBM rather than recomputed
+// by neighbouring threads: the stage kernels read their stencil from scratch
 // fields laid out like the state (x fastest, coalesced across a warp).
+//
+// Precision.  The state, the dt reduction and the flux-divergence update are
+// always FP64.  The reconstruction, tracing, CTU corrections and Riemann
+// solves (the templated stage kernels, compute type R) run in FP64 for
+// HYDRO_FP64 boxes and in FP32 for HYDRO_MIXED boxes, whose scratch fields are
+// FP32 (half the bytes).  Each face flux is a single value used by both
+// neighbours, so the FP64 update conserves mass, momentum and energy to FP64
+// round-off in both forms.
 //
 // Stages (paper §3: limited slopes from neighbours, then a polynomial
 // reconstruction; the published methods are cited per stage):
 //   k_fill       ghost zones from the boundary conditions (x, then y, then z)
-//   k_prim       conserved -> primitive + EOS; per-box max signal speed for dt
+//   k_prim       conserved -> primitive + EOS (FP64); per-box max signal speed
 //   k_dt         dt = cfl / max((|u_d|+c)/dx_d)
 //   k_flatten    CW84 §4 shock flattening coefficient (max over directions)
 //   k_slopes     CW84 limited slopes, once per zone and axis
@@ -18,7 +26,7 @@
 //   k_riemann    HLLC normal fluxes F0_d on the extended face region
 //   k_ctu1       3D CTU stage 1: dt/(3dx_e) transverse corrections + HLLC
 //   k_ctu2       3D CTU stage 2: dt/(2dx) corrections + HLLC -> final fluxes
-//   k_update     conservative flux-divergence update + physicality flag
+//   k_update     conservative flux-divergence update (FP64) + physicality flag
 #include <algorithm>
 #include <cmath>
 
@@ -34,6 +42,18 @@ constexpr int TPB = 128;
 template <int D>
 __device__ __forceinline__ constexpr int comp(int m) {
   return (m == 0 || m == 4) ? m : 1 + (D + m - 1) % 3;
+}
+
+template <typename R>
+__device__ __forceinline__ bool box_uses(const DevBox& b);
+template <>
+__device__ __forceinline__ bool box_uses<double>(const DevBox& b) { return b.precision == HYDRO_FP64; }
+template <>
+__device__ __forceinline__ bool box_uses<float>(const DevBox& b) { return b.precision == HYDRO_MIXED; }
+
+template <typename R>
+__device__ __forceinline__ R* fields(unsigned char* work, const DevBox& b) {
+  return reinterpret_cast<R*>(work + b.work_off);
 }
 
 __device__ __forceinline__ long long zone(const DevBox& b, int i, int j, int k) {
@@ -88,8 +108,10 @@ __global__ void __launch_bounds__(256) k_fill(const DevBox* __restrict__ boxes, 
 }
 
 // ------------------------------------------------- conserved -> primitive, dt
+// FP64 arithmetic for every box (the dt reduction needs it); the primitive
+// fields are stored in the box's compute type.
 __global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, const double* __restrict__ state,
-                                              double* __restrict__ work, BoxRt* __restrict__ rt) {
+                                              unsigned char* __restrict__ work, BoxRt* __restrict__ rt) {
   const int bi = blockIdx.y;
   const DevBox& b = boxes[bi];
   int lo[3] = {-NG, -NG, -NG};
@@ -100,7 +122,6 @@ __global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, 
     const long long Z = zone(b, c[0], c[1], c[2]);
     const long long vs = b.vs;
     const double* U = state + b.state_off;
-    double* W = work + b.work_off;
     double rho = U[Z];
     if (rho < SMALL_DENS) rho = SMALL_DENS;
     const double ir = nr_rcp(rho);
@@ -108,12 +129,23 @@ __global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, 
     double p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
     if (p < SMALL_PRES) p = SMALL_PRES;
     const double cs = nr_sqrt(b.gamma * p * ir);
-    W[Z] = rho;
-    W[vs + Z] = u;
-    W[2 * vs + Z] = v;
-    W[3 * vs + Z] = w;
-    W[4 * vs + Z] = p;
-    W[FLD_C * vs + Z] = cs;
+    if (b.precision == HYDRO_FP64) {
+      double* W = fields<double>(work, b);
+      W[Z] = rho;
+      W[vs + Z] = u;
+      W[2 * vs + Z] = v;
+      W[3 * vs + Z] = w;
+      W[4 * vs + Z] = p;
+      W[FLD_C * vs + Z] = cs;
+    } else {
+      float* W = fields<float>(work, b);
+      W[Z] = (float)rho;
+      W[vs + Z] = (float)u;
+      W[2 * vs + Z] = (float)v;
+      W[3 * vs + Z] = (float)w;
+      W[4 * vs + Z] = (float)p;
+      W[FLD_C * vs + Z] = (float)cs;
+    }
     if (c[0] >= 0 && c[0] < b.n[0] && c[1] >= 0 && c[1] < b.n[1] && c[2] >= 0 && c[2] < b.n[2]) {
       double s = fmax(fmax((fabs(u) + cs) * b.idx[0], (fabs(v) + cs) * b.idx[1]), (fabs(w) + cs) * b.idx[2]);
       sbits = (unsigned long long)__double_as_longlong(s);
@@ -144,29 +176,31 @@ __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, i
 }
 
 // ---------------------------------------------------------------- flattening
-__device__ __forceinline__ double flat_tilde(const double* __restrict__ p, const double* __restrict__ un,
-                                             long long Z, long long s) {
-  const double pp = p[Z + s], pm = p[Z - s];
-  const double dp1 = pp - pm;
-  if (!(fabs(dp1) > FLAT_EPS * fmin(pp, pm)) || !(un[Z - s] - un[Z + s] > 0.0)) return 0.0;
-  const double dp2 = p[Z + 2 * s] - p[Z - 2 * s];
-  if (dp2 == 0.0) return 0.0;
-  return fmin(1.0, fmax(0.0, FLAT_OMEGA2 * (dp1 / dp2 - FLAT_OMEGA1)));
+template <typename R>
+__device__ __forceinline__ R flat_tilde(const R* __restrict__ p, const R* __restrict__ un, long long Z, long long s) {
+  const R pp = p[Z + s], pm = p[Z - s];
+  const R dp1 = pp - pm;
+  if (!(fabs(dp1) > R(FLAT_EPS) * fmin(pp, pm)) || !(un[Z - s] - un[Z + s] > R(0))) return R(0);
+  const R dp2 = p[Z + 2 * s] - p[Z - 2 * s];
+  if (dp2 == R(0)) return R(0);
+  return fmin(R(1), fmax(R(0), R(FLAT_OMEGA2) * (dp1 / dp2 - R(FLAT_OMEGA1))));
 }
 
-__global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
-  const double* p = W + 4 * b.vs;
-  double f = 0.0;
+  R* W = fields<R>(work, b);
+  const R* p = W + 4 * b.vs;
+  R f = R(0);
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    const double* un = W + (1 + d) * b.vs;
+    const R* un = W + (1 + d) * b.vs;
     const long long s = b.s[d];
-    const long long sh = p[Z + s] - p[Z - s] >= 0.0 ? s : -s;
+    const long long sh = p[Z + s] - p[Z - s] >= R(0) ? s : -s;
     f = fmax(f, fmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s)));
   }
   W[FLD_CHI * b.vs + Z] = f;
@@ -175,115 +209,119 @@ __global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxe
 // ------------------------------------------------------------- PPM + tracing
 // van Leer limited slope at a0 (CW84 eq. 1.8); the sign test and the minimum
 // run on the integer pipe (magnitudes order like their bit patterns).
-__device__ __forceinline__ double vl_slope(double am, double a0, double ap) {
-  const double dl = a0 - am, dr = ap - a0;
-  if (!same_sign(dl, dr)) return 0.0;
-  const double dc = 0.5 * (ap - am);
-  long long m = dbits(fabs(dc));
-  m = min(m, dbits(2.0 * fabs(dl)));
-  m = min(m, dbits(2.0 * fabs(dr)));
-  return copysign(__longlong_as_double(m), dc);
+template <typename R>
+__device__ __forceinline__ R vl_slope(R am, R a0, R ap) {
+  const R dl = a0 - am, dr = ap - a0;
+  if (!same_sign(dl, dr)) return R(0);
+  const R dc = R(0.5) * (ap - am);
+  auto m = dbits(fabs(dc));
+  m = min(m, dbits(R(2) * fabs(dl)));
+  m = min(m, dbits(R(2) * fabs(dr)));
+  return copysign(from_bits(m), dc);
 }
 
 // Limited slopes of the five normal-frame variables of axis D, once per zone
 // of [-2, n_D+1] along D and [-1, n] across it.
-template <int D>
-__device__ __forceinline__ void slopes_zone(const DevBox& b, double* __restrict__ W, long long Z) {
+template <typename R, int D>
+__device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, long long Z) {
   const long long vs = b.vs, s = b.s[D];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
-    const double* a = W + comp<D>(m) * vs + Z;
+    const R* a = W + comp<D>(m) * vs + Z;
     W[(FLD_DQ + 5 * D + m) * vs + Z] = vl_slope(a[-s], a[0], a[s]);
   }
 }
 
-__global__ void __launch_bounds__(256) k_slopes(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_slopes(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   const int d = blockIdx.z;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   lo[d] = -2;
   ext[d] = b.n[d] + 4;
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
+  R* W = fields<R>(work, b);
   switch (d) {
-    case 0: slopes_zone<0>(b, W, Z); break;
-    case 1: slopes_zone<1>(b, W, Z); break;
-    default: slopes_zone<2>(b, W, Z); break;
+    case 0: slopes_zone<R, 0>(b, W, Z); break;
+    case 1: slopes_zone<R, 1>(b, W, Z); break;
+    default: slopes_zone<R, 2>(b, W, Z); break;
   }
 }
 
 // Parabola of zone value a0 with neighbours am1, ap1 and limited slopes
 // dm1, d0, dp1: interface values (CW84 eq. 1.6), monotonicity limiter
 // (eq. 1.10) with its tests on the integer pipe, then flattening by f.
-__device__ __forceinline__ void parabola(double am1, double a0, double ap1, double dm1, double d0, double dp1,
-                                         double f, double& L, double& R) {
-  L = am1 + 0.5 * (a0 - am1) - (d0 - dm1) * (1.0 / 6.0);
-  R = a0 + 0.5 * (ap1 - a0) - (dp1 - d0) * (1.0 / 6.0);
-  if (!same_sign(R - a0, a0 - L)) {
+template <typename R>
+__device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1, R f, R& L, R& Rt) {
+  L = am1 + R(0.5) * (a0 - am1) - (d0 - dm1) * R(1.0 / 6.0);
+  Rt = a0 + R(0.5) * (ap1 - a0) - (dp1 - d0) * R(1.0 / 6.0);
+  if (!same_sign(Rt - a0, a0 - L)) {
     L = a0;
-    R = a0;
+    Rt = a0;
   } else {
-    const double dA = R - L;
-    const double t1 = dA * (a0 - 0.5 * (L + R));
-    const double t2 = dA * dA * (1.0 / 6.0);
-    if (dgt(t1, t2)) L = 3.0 * a0 - 2.0 * R;
-    else if (dgt(-t2, t1)) R = 3.0 * a0 - 2.0 * L;
+    const R dA = Rt - L;
+    const R t1 = dA * (a0 - R(0.5) * (L + Rt));
+    const R t2 = dA * dA * R(1.0 / 6.0);
+    if (dgt(t1, t2)) L = R(3) * a0 - R(2) * Rt;
+    else if (dgt(-t2, t1)) Rt = R(3) * a0 - R(2) * L;
   }
   if (is_pos(f)) {
-    L = f * a0 + (1.0 - f) * L;
-    R = f * a0 + (1.0 - f) * R;
+    L = f * a0 + (R(1) - f) * L;
+    Rt = f * a0 + (R(1) - f) * Rt;
   }
 }
 
-template <int D>
-__device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__ W, long long Z, double dtdx) {
+template <typename R, int D>
+__device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
   const long long vs = b.vs, s = b.s[D];
-  const double f = W[FLD_CHI * vs + Z];
-  double a0[5], aL[5], aR[5];
+  const R f = W[FLD_CHI * vs + Z];
+  R a0[5], aL[5], aR[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
-    const double* a = W + comp<D>(m) * vs + Z;
-    const double* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
+    const R* a = W + comp<D>(m) * vs + Z;
+    const R* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
     a0[m] = a[0];
     parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
   }
-  double dA[5], a6[5];
+  R dA[5], a6[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     dA[m] = aR[m] - aL[m];
-    a6[m] = 6.0 * (a0[m] - 0.5 * (aL[m] + aR[m]));
+    a6[m] = R(6) * (a0[m] - R(0.5) * (aL[m] + aR[m]));
   }
-  const double cs = W[FLD_C * vs + Z];
-  const double rho = a0[0], u = a0[1];
-  const double ic = nr_rcp(cs);
-  const double rc = 0.5 * rho * ic;   // rho / 2c
-  const double i2c2 = 0.5 * ic * ic;  // 1 / 2c^2
-  const double ic2 = ic * ic;         // 1 / c^2
-  const double cr = cs * nr_rcp(rho); // c / rho
-  const double c2 = cs * cs;
-  const double lm = u - cs, lp = u + cs;
+  const R cs = W[FLD_C * vs + Z];
+  const R rho = a0[0], u = a0[1];
+  const R ic = nr_rcp(cs);
+  const R rc = R(0.5) * rho * ic;   // rho / 2c
+  const R i2c2 = R(0.5) * ic * ic;  // 1 / 2c^2
+  const R ic2 = ic * ic;            // 1 / c^2
+  const R cr = cs * nr_rcp(rho);    // c / rho
+  const R c2 = cs * cs;
+  const R lm = u - cs, lp = u + cs;
+  const R two3 = R(2.0 / 3.0);
 
-  double out[5];
+  R out[5];
   // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
   if (is_pos(lp)) {
-    double sg = lp * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
-    double ref[5];
+    R sg = lp * dtdx, h1 = R(0.5) * sg, h2 = R(1) - sg * two3;
+    R ref[5];
 #pragma unroll
     for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * a6[m]);
-    double bm = 0.0, b0 = 0.0;
+    R bm = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
     if (is_pos(lm)) {
-      sg = lm * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
-      const double du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * a6[1]));
-      const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      sg = lm * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
+      const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * a6[1]));
+      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
       bm = -rc * du + i2c2 * dp;
     }
     if (is_pos(u)) {
-      sg = u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
-      const double dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * a6[0]));
-      const double dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      sg = u * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
+      const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * a6[0]));
+      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
       b0 = dr - ic2 * dp;
       out[2] = aR[2] - h1 * (dA[2] - h2 * a6[2]);
       out[3] = aR[3] - h1 * (dA[3] - h2 * a6[3]);
@@ -295,30 +333,30 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
 #pragma unroll
     for (int m = 0; m < 5; m++) out[m] = a0[m];
   }
-  if (dgt(SMALL_DENS, out[0])) out[0] = SMALL_DENS;
-  if (dgt(SMALL_PRES, out[4])) out[4] = SMALL_PRES;
+  if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
+  if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
   if (is_neg(lm)) {
-    double sg = -lm * dtdx, h1 = 0.5 * sg, h2 = 1.0 - sg * (2.0 / 3.0);
-    double ref[5];
+    R sg = -lm * dtdx, h1 = R(0.5) * sg, h2 = R(1) - sg * two3;
+    R ref[5];
 #pragma unroll
     for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * a6[m]);
-    double bp = 0.0, b0 = 0.0;
+    R bp = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
     if (is_neg(lp)) {
-      sg = -lp * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
-      const double du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * a6[1]));
-      const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      sg = -lp * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
+      const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * a6[1]));
+      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
       bp = rc * du + i2c2 * dp;
     }
     if (is_neg(u)) {
-      sg = -u * dtdx; h1 = 0.5 * sg; h2 = 1.0 - sg * (2.0 / 3.0);
-      const double dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * a6[0]));
-      const double dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      sg = -u * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
+      const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * a6[0]));
+      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
       b0 = dr - ic2 * dp;
       out[2] = aL[2] + h1 * (dA[2] + h2 * a6[2]);
       out[3] = aL[3] + h1 * (dA[3] + h2 * a6[3]);
@@ -330,24 +368,26 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, double* __restrict__
 #pragma unroll
     for (int m = 0; m < 5; m++) out[m] = a0[m];
   }
-  if (dgt(SMALL_DENS, out[0])) out[0] = SMALL_DENS;
-  if (dgt(SMALL_PRES, out[4])) out[4] = SMALL_PRES;
+  if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
+  if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
 }
 
+template <typename R>
 __global__ void __launch_bounds__(TPB) k_trace(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                               double* __restrict__ work) {
+                                               unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
+  R* W = fields<R>(work, b);
   const double dt = rt[blockIdx.y].dt;
   switch (blockIdx.z) {
-    case 0: trace_zone<0>(b, W, Z, dt * b.idx[0]); break;
-    case 1: trace_zone<1>(b, W, Z, dt * b.idx[1]); break;
-    default: trace_zone<2>(b, W, Z, dt * b.idx[2]); break;
+    case 0: trace_zone<R, 0>(b, W, Z, R(dt * b.idx[0])); break;
+    case 1: trace_zone<R, 1>(b, W, Z, R(dt * b.idx[1])); break;
+    default: trace_zone<R, 2>(b, W, Z, R(dt * b.idx[2])); break;
   }
 }
 
@@ -360,40 +400,41 @@ __global__ void __launch_bounds__(TPB) k_trace(const DevBox* __restrict__ boxes,
 // 1/rho, c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed)
 // and three reciprocals; wave-speed min/max and sign tests run on the integer
 // pipe.
-__device__ __forceinline__ void hllc(const double* L, const double* R, double gamma, double igm1, double* F) {
-  const double gm1 = gamma - 1.0;
-  const double rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
-  const double rr = R[0], ur = R[1], vr = R[2], wr = R[3], pr = R[4];
-  const double rsl = nr_rsqrt(rl), rsr = nr_rsqrt(rr);  // 1/sqrt(rho)
-  const double sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
-  const double irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
-  const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
-  const double El = pl * igm1 + 0.5 * rl * (ul * ul + vl * vl + wl * wl);
-  const double Er = pr * igm1 + 0.5 * rr * (ur * ur + vr * vr + wr * wr);
-  const double iw = nr_rcp(sl + sr);
-  const double wgl = sl * iw, wgr = sr * iw;
-  const double ut = wgl * ul + wgr * ur;
-  const double vt = wgl * vl + wgr * vr;
-  const double wt = wgl * wl + wgr * wr;
-  const double Ht = wgl * ((El + pl) * irl) + wgr * ((Er + pr) * irr);
-  const double ct2 = gm1 * (Ht - 0.5 * (ut * ut + vt * vt + wt * wt));
-  double SL, SR;
+template <typename R>
+__device__ __forceinline__ void hllc(const R* L, const R* Rs, R gamma, R igm1, R* F) {
+  const R gm1 = gamma - R(1);
+  const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
+  const R rr = Rs[0], ur = Rs[1], vr = Rs[2], wr = Rs[3], pr = Rs[4];
+  const R rsl = nr_rsqrt(rl), rsr = nr_rsqrt(rr);  // 1/sqrt(rho)
+  const R sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
+  const R irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
+  const R gpl = gamma * pl, gpr = gamma * pr;
+  const R cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
+  const R El = pl * igm1 + R(0.5) * rl * (ul * ul + vl * vl + wl * wl);
+  const R Er = pr * igm1 + R(0.5) * rr * (ur * ur + vr * vr + wr * wr);
+  const R iw = nr_rcp(sl + sr);
+  const R wgl = sl * iw, wgr = sr * iw;
+  const R ut = wgl * ul + wgr * ur;
+  const R vt = wgl * vl + wgr * vr;
+  const R wt = wgl * wl + wgr * wr;
+  const R Ht = wgl * ((El + pl) * irl) + wgr * ((Er + pr) * irr);
+  const R ct2 = gm1 * (Ht - R(0.5) * (ut * ut + vt * vt + wt * wt));
+  R SL, SR;
   if (is_pos(ct2)) {
-    const double ct = nr_sqrt(ct2);
+    const R ct = nr_sqrt(ct2);
     SL = dmin(ul - cl, ut - ct);
     SR = dmax(ur + cr, ut + ct);
   } else {
     SL = dmin(ul - cl, ur - cr);
     SR = dmax(ul + cl, ur + cr);
   }
-  const double ml = rl * (SL - ul), mr = rr * (SR - ur);
-  const double Ss = (pr - pl + ml * ul - mr * ur) * nr_rcp(ml - mr);
+  const R ml = rl * (SL - ul), mr = rr * (SR - ur);
+  const R Ss = (pr - pl + ml * ul - mr * ur) * nr_rcp(ml - mr);
   const bool left = is_nonneg(Ss);
-  const double rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
-  const double pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
-  const double irK = left ? irl : irr;
-  const double mu = rK * uK;
+  const R rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
+  const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
+  const R irK = left ? irl : irr;
+  const R mu = rK * uK;
   F[0] = mu;
   F[1] = mu * uK + pK;
   F[2] = mu * vK;
@@ -402,10 +443,10 @@ __device__ __forceinline__ void hllc(const double* L, const double* R, double ga
   const bool supersonic = left ? is_nonneg(SL) : !is_pos(SR);
   if (!supersonic) {
     // fac = mK / (SK - S*) and pK / mK from one reciprocal of mK (SK - S*)
-    const double den = SK - Ss;
-    const double r = nr_rcp(mK * den);
-    const double fac = mK * mK * r;
-    const double eK = EK * irK + (Ss - uK) * (Ss + pK * den * r);
+    const R den = SK - Ss;
+    const R r = nr_rcp(mK * den);
+    const R fac = mK * mK * r;
+    const R eK = EK * irK + (Ss - uK) * (Ss + pK * den * r);
     F[0] += SK * (fac - rK);
     F[1] += SK * (fac * Ss - mu);
     F[2] += SK * (fac * vK - rK * vK);
@@ -414,9 +455,9 @@ __device__ __forceinline__ void hllc(const double* L, const double* R, double ga
   }
 }
 
-template <int D>
-__device__ __forceinline__ void load_face_states(const double* __restrict__ W, long long vs, long long Z, long long sD,
-                                                 double* qL, double* qR) {
+template <typename R, int D>
+__device__ __forceinline__ void load_face_states(const R* __restrict__ W, long long vs, long long Z, long long sD,
+                                                 R* qL, R* qR) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     qL[m] = W[(FLD_QP + 5 * D + m) * vs + Z - sD];
@@ -424,33 +465,35 @@ __device__ __forceinline__ void load_face_states(const double* __restrict__ W, l
   }
 }
 
-template <int D>
-__device__ __forceinline__ void store_flux(double* __restrict__ dst, long long vs, long long Z, const double* Fn) {
+template <typename R, int D>
+__device__ __forceinline__ void store_flux(R* __restrict__ dst, long long vs, long long Z, const R* Fn) {
 #pragma unroll
   for (int m = 0; m < 5; m++) dst[comp<D>(m) * vs + Z] = Fn[m];
 }
 
-template <int D>
-__device__ __forceinline__ void riemann_face(const DevBox& b, double* __restrict__ W, long long Z) {
-  double qL[5], qR[5], Fn[5];
-  load_face_states<D>(W, b.vs, Z, b.s[D], qL, qR);
-  hllc(qL, qR, b.gamma, b.igm1, Fn);
-  store_flux<D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
+template <typename R, int D>
+__device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
+  R qL[5], qR[5], Fn[5];
+  load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, qR);
+  hllc(qL, qR, R(b.gamma), R(b.igm1), Fn);
+  store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
-__global__ void __launch_bounds__(TPB) k_riemann(const DevBox* __restrict__ boxes, double* __restrict__ work) {
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_riemann(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   const int d = blockIdx.z;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   lo[d] = 0;
   ext[d] = b.n[d] + 1;
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
+  R* W = fields<R>(work, b);
   switch (d) {
-    case 0: riemann_face<0>(b, W, Z); break;
-    case 1: riemann_face<1>(b, W, Z); break;
-    default: riemann_face<2>(b, W, Z); break;
+    case 0: riemann_face<R, 0>(b, W, Z); break;
+    case 1: riemann_face<R, 1>(b, W, Z); break;
+    default: riemann_face<R, 2>(b, W, Z); break;
   }
 }
 
@@ -458,15 +501,15 @@ __global__ void __launch_bounds__(TPB) k_riemann(const DevBox* __restrict__ boxe
 // Face state q (normal frame of D) of the zone Z -> conserved, minus
 // fac_t * (flux difference across zone Z along stride s_t) for each term t,
 // -> primitive.  A result with rho <= 0 or p <= 0 keeps the uncorrected state.
-template <int D, int NT>
-__device__ __forceinline__ void correct(double* q, const double* const* Fb, const long long* st, const double* fac,
-                                        long long vs, long long Z, double gamma, double igm1) {
-  double U[5];
+template <typename R, int D, int NT>
+__device__ __forceinline__ void correct(R* q, const R* const* Fb, const long long* st, const R* fac, long long vs,
+                                        long long Z, R gamma, R igm1) {
+  R U[5];
   U[0] = q[0];
   U[1] = q[0] * q[1];
   U[2] = q[0] * q[2];
   U[3] = q[0] * q[3];
-  U[4] = q[4] * igm1 + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  U[4] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const long long off = comp<D>(m) * vs + Z;
@@ -474,39 +517,41 @@ __device__ __forceinline__ void correct(double* q, const double* const* Fb, cons
     for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * (Fb[t][off + st[t]] - Fb[t][off]);
   }
   if (is_pos(U[0])) {
-    const double ir = nr_rcp(U[0]);
-    const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    const double p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w));
+    const R ir = nr_rcp(U[0]);
+    const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const R p = (gamma - R(1)) * (U[4] - R(0.5) * U[0] * (u * u + v * v + w * w));
     if (is_pos(p)) {
       q[0] = U[0];
       q[1] = u;
       q[2] = v;
       q[3] = w;
-      q[4] = dgt(SMALL_PRES, p) ? SMALL_PRES : p;
+      q[4] = dgt(R(SMALL_PRES), p) ? R(SMALL_PRES) : p;
     }
   }
 }
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
 
-template <int D, int E>
-__device__ __forceinline__ void ctu1_face(const DevBox& b, double* __restrict__ W, long long Z, double dt) {
+template <typename R, int D, int E>
+__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, double dt) {
   const long long vs = b.vs, sD = b.s[D];
-  const double igm1 = b.igm1;
-  double qL[5], qR[5], Fn[5];
-  load_face_states<D>(W, vs, Z, sD, qL, qR);
-  const double* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
+  const R gamma = R(b.gamma), igm1 = R(b.igm1);
+  R qL[5], qR[5], Fn[5];
+  load_face_states<R, D>(W, vs, Z, sD, qL, qR);
+  const R* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
   const long long st[1] = {b.s[E]};
-  const double fac[1] = {dt * b.idx[E] * (1.0 / 3.0)};
-  correct<D, 1>(qL, Fb, st, fac, vs, Z - sD, b.gamma, igm1);
-  correct<D, 1>(qR, Fb, st, fac, vs, Z, b.gamma, igm1);
-  hllc(qL, qR, b.gamma, igm1, Fn);
-  store_flux<D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
+  const R fac[1] = {R(dt * b.idx[E] * (1.0 / 3.0))};
+  correct<R, D, 1>(qL, Fb, st, fac, vs, Z - sD, gamma, igm1);
+  correct<R, D, 1>(qR, Fb, st, fac, vs, Z, gamma, igm1);
+  hllc(qL, qR, gamma, igm1, Fn);
+  store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
 }
 
+template <typename R>
 __global__ void __launch_bounds__(TPB) k_ctu1(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                              double* __restrict__ work) {
+                                              unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   const int p = blockIdx.z;  // pair slot: xy xz yx yz zx zy
   const int d = p / 2, r = p % 2;
   const int e = r == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);
@@ -517,76 +562,94 @@ __global__ void __launch_bounds__(TPB) k_ctu1(const DevBox* __restrict__ boxes, 
   lo[f] = -1; ext[f] = b.n[f] + 2;
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
+  R* W = fields<R>(work, b);
   const double dt = rt[blockIdx.y].dt;
   switch (p) {
-    case 0: ctu1_face<0, 1>(b, W, Z, dt); break;
-    case 1: ctu1_face<0, 2>(b, W, Z, dt); break;
-    case 2: ctu1_face<1, 0>(b, W, Z, dt); break;
-    case 3: ctu1_face<1, 2>(b, W, Z, dt); break;
-    case 4: ctu1_face<2, 0>(b, W, Z, dt); break;
-    default: ctu1_face<2, 1>(b, W, Z, dt); break;
+    case 0: ctu1_face<R, 0, 1>(b, W, Z, dt); break;
+    case 1: ctu1_face<R, 0, 2>(b, W, Z, dt); break;
+    case 2: ctu1_face<R, 1, 0>(b, W, Z, dt); break;
+    case 3: ctu1_face<R, 1, 2>(b, W, Z, dt); break;
+    case 4: ctu1_face<R, 2, 0>(b, W, Z, dt); break;
+    default: ctu1_face<R, 2, 1>(b, W, Z, dt); break;
   }
 }
 
-template <int D>
-__device__ __forceinline__ void ctu2_face(const DevBox& b, double* __restrict__ W, long long Z, double dt) {
+template <typename R, int D>
+__device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, long long Z, double dt, bool wall) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
   const long long vs = b.vs, sD = b.s[D];
-  const double igm1 = b.igm1;
-  double qL[5], qR[5], Fn[5];
-  load_face_states<D>(W, vs, Z, sD, qL, qR);
-  const double* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
+  const R gamma = R(b.gamma), igm1 = R(b.igm1);
+  R qL[5], qR[5], Fn[5];
+  load_face_states<R, D>(W, vs, Z, sD, qL, qR);
+  const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
-  const double fac[2] = {0.5 * dt * b.idx[E], 0.5 * dt * b.idx[F]};
-  correct<D, 2>(qL, Fb, st, fac, vs, Z - sD, b.gamma, igm1);
-  correct<D, 2>(qR, Fb, st, fac, vs, Z, b.gamma, igm1);
-  hllc(qL, qR, b.gamma, igm1, Fn);
-  store_flux<D>(W + (FLD_F + 5 * D) * vs, vs, Z, Fn);
+  const R fac[2] = {R(0.5 * dt * b.idx[E]), R(0.5 * dt * b.idx[F])};
+  correct<R, D, 2>(qL, Fb, st, fac, vs, Z - sD, gamma, igm1);
+  correct<R, D, 2>(qR, Fb, st, fac, vs, Z, gamma, igm1);
+  hllc(qL, qR, gamma, igm1, Fn);
+  if (wall) {
+    // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
+    Fn[0] = R(0);
+    Fn[2] = R(0);
+    Fn[3] = R(0);
+    Fn[4] = R(0);
+  }
+  store_flux<R, D>(W + (FLD_F + 5 * D) * vs, vs, Z, Fn);
 }
 
+template <typename R>
 __global__ void __launch_bounds__(TPB) k_ctu2(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                              double* __restrict__ work) {
+                                              unsigned char* __restrict__ work) {
   const DevBox& b = boxes[blockIdx.y];
+  if (!box_uses<R>(b)) return;
   const int d = blockIdx.z;
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
   ext[d] = b.n[d] + 1;
   if (!decode(tid(), lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
-  double* W = work + b.work_off;
+  R* W = fields<R>(work, b);
   const double dt = rt[blockIdx.y].dt;
+  const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT) ||
+                    (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT);
   switch (d) {
-    case 0: ctu2_face<0>(b, W, Z, dt); break;
-    case 1: ctu2_face<1>(b, W, Z, dt); break;
-    default: ctu2_face<2>(b, W, Z, dt); break;
+    case 0: ctu2_face<R, 0>(b, W, Z, dt, wall); break;
+    case 1: ctu2_face<R, 1>(b, W, Z, dt, wall); break;
+    default: ctu2_face<R, 2>(b, W, Z, dt, wall); break;
   }
 }
 
 // --------------------------------------------------------------------- update
-__global__ void __launch_bounds__(256) k_update(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt,
-                                                double* __restrict__ state, const double* __restrict__ work) {
-  const int bi = blockIdx.y;
-  const DevBox& b = boxes[bi];
-  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
-  const long long Z = zone(b, c[0], c[1], c[2]);
+// FP64 for every box; the fluxes are read in the box's compute type.
+template <typename R>
+__device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict__ U, const R* __restrict__ W,
+                                            long long Z, double dt, double* nu) {
   const long long vs = b.vs;
-  double* U = state + b.state_off;
-  const double* W = work + b.work_off;
-  const double dt = rt[bi].dt;
   const double dtdx[3] = {dt * b.idx[0], dt * b.idx[1], dt * b.idx[2]};
-  double nu[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     double val = U[v * vs + Z];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-      const double* F = W + (FLD_F + 5 * d + v) * vs;
-      val = val - dtdx[d] * (F[Z + b.s[d]] - F[Z]);
+      const R* F = W + (FLD_F + 5 * d + v) * vs;
+      val = val - dtdx[d] * ((double)F[Z + b.s[d]] - (double)F[Z]);
     }
     nu[v] = val;
     U[v * vs + Z] = val;
   }
+}
+
+__global__ void __launch_bounds__(256) k_update(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt,
+                                                double* __restrict__ state, unsigned char* __restrict__ work) {
+  const int bi = blockIdx.y;
+  const DevBox& b = boxes[bi];
+  int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
+  if (!decode(tid(), lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
+  double* U = state + b.state_off;
+  const double dt = rt[bi].dt;
+  double nu[5];
+  if (b.precision == HYDRO_FP64) update_zone(b, U, fields<double>(work, b), Z, dt, nu);
+  else update_zone(b, U, fields<float>(work, b), Z, dt, nu);
   const double kin = 0.5 * (nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3]) / nu[0];
   const double p = (b.gamma - 1.0) * (nu[4] - kin);
   if (!(nu[0] > 0.0) || !(p > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
@@ -646,20 +709,87 @@ long long max_volume_faces(const Plan& p, int fext) {
   return m;
 }
 
+// max over boxes and axes of a region with axis a extended by `along` and the
+// two other axes by `across`
+long long max_volume_axis(const Plan& p, int along, int across) {
+  long long m = 0;
+  for (int i = 0; i < p.nboxes; i++) {
+    const hydro_box_desc& d = p.boxes[i].d;
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; a++)
+      m = std::max(m, (long long)(n[a] + along) * (n[(a + 1) % 3] + across) * (n[(a + 2) % 3] + across));
+  }
+  return m;
+}
+
 dim3 grid_for(long long vol, int tpb, int nboxes, int z = 1) {
   long long bx = (vol + tpb - 1) / tpb;
   if (bx < 1) bx = 1;
   return dim3((unsigned)bx, (unsigned)nboxes, (unsigned)z);
 }
 
+// Launches the templated stage kernel for each compute type present in the plan.
+template <template <typename> class K>
+cudaError_t per_precision(const Plan& p, cudaStream_t s, int* launched) {
+  if (p.has_fp64) {
+    K<double>::go(p, s);
+    ++*launched;
+  }
+  if (p.has_mixed) {
+    K<float>::go(p, s);
+    ++*launched;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "slopes", "trace",
                                            "riemann", "ctu1", "ctu2", "update"};
-const int STAGE_KERNELS[NSTAGES] = {3, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+
+namespace {
+template <typename R>
+struct LFlatten {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_flatten<R><<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes), TPB, 0, s>>>(p.dboxes, p.work);
+  }
+};
+template <typename R>
+struct LSlopes {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_slopes<R><<<grid_for(max_volume_axis(p, 4, 2), 256, p.nboxes, 3), 256, 0, s>>>(p.dboxes, p.work);
+  }
+};
+template <typename R>
+struct LTrace {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_trace<R><<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
+  }
+};
+template <typename R>
+struct LRiemann {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_riemann<R><<<grid_for(max_volume_axis(p, 1, 2), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.work);
+  }
+};
+template <typename R>
+struct LCtu1 {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_ctu1<R><<<grid_for(max_volume_faces(p, 2), TPB, p.nboxes, 6), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
+  }
+};
+template <typename R>
+struct LCtu2 {
+  static void go(const Plan& p, cudaStream_t s) {
+    k_ctu2<R><<<grid_for(max_volume_faces(p, 0), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
+  }
+};
+}  // namespace
 
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
-                         int advance) {
+                         int advance, int* launched) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
   switch (st) {
     case ST_FILL: {
       long long vx = 0, vy = 0, vz = 0;
@@ -672,59 +802,38 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
       k_fill<0><<<grid_for(vx, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
       k_fill<1><<<grid_for(vy, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
       k_fill<2><<<grid_for(vz, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
+      n = 3;
+      e = cudaGetLastError();
       break;
     }
     case ST_PRIM:
       k_prim<<<grid_for(max_volume(p, 2 * NG, 2 * NG, 2 * NG), 256, p.nboxes), 256, 0, stream>>>(
           p.dboxes, p.state, p.work, p.rt);
+      n = 1;
+      e = cudaGetLastError();
       break;
     case ST_DT:
       k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
+      n = 1;
+      e = cudaGetLastError();
       break;
-    case ST_FLATTEN:
-      k_flatten<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes), TPB, 0, stream>>>(p.dboxes, p.work);
-      break;
-    case ST_SLOPES: {
-      // slope region: axis d has n+4 zones, the transverse axes n+2
-      long long vs0 = 0;
-      for (int i = 0; i < p.nboxes; i++) {
-        const hydro_box_desc& d = p.boxes[i].d;
-        const int n[3] = {d.nx, d.ny, d.nz};
-        for (int a = 0; a < 3; a++)
-          vs0 = std::max(vs0, (long long)(n[a] + 4) * (n[(a + 1) % 3] + 2) * (n[(a + 2) % 3] + 2));
-      }
-      k_slopes<<<grid_for(vs0, 256, p.nboxes, 3), 256, 0, stream>>>(p.dboxes, p.work);
-      break;
-    }
-    case ST_TRACE:
-      k_trace<<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
-      break;
-    case ST_RIEMANN: {
-      // normal faces: axis d has n+1 faces, both transverse axes n+2 zones
-      long long vf0 = 0;
-      for (int i = 0; i < p.nboxes; i++) {
-        const hydro_box_desc& d = p.boxes[i].d;
-        const int n[3] = {d.nx, d.ny, d.nz};
-        for (int a = 0; a < 3; a++)
-          vf0 = std::max(vf0, (long long)(n[a] + 1) * (n[(a + 1) % 3] + 2) * (n[(a + 2) % 3] + 2));
-      }
-      k_riemann<<<grid_for(vf0, TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.work);
-      break;
-    }
-    case ST_CTU1:
-      k_ctu1<<<grid_for(max_volume_faces(p, 2), TPB, p.nboxes, 6), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
-      break;
-    case ST_CTU2:
-      k_ctu2<<<grid_for(max_volume_faces(p, 0), TPB, p.nboxes, 3), TPB, 0, stream>>>(p.dboxes, p.rt, p.work);
-      break;
+    case ST_FLATTEN: e = per_precision<LFlatten>(p, stream, &n); break;
+    case ST_SLOPES: e = per_precision<LSlopes>(p, stream, &n); break;
+    case ST_TRACE: e = per_precision<LTrace>(p, stream, &n); break;
+    case ST_RIEMANN: e = per_precision<LRiemann>(p, stream, &n); break;
+    case ST_CTU1: e = per_precision<LCtu1>(p, stream, &n); break;
+    case ST_CTU2: e = per_precision<LCtu2>(p, stream, &n); break;
     case ST_UPDATE:
       k_update<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.rt, p.state,
                                                                                    p.work);
+      n = 1;
+      e = cudaGetLastError();
       break;
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  if (launched) *launched = n;
+  return e;
 }
 
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream) {

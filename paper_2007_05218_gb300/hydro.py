@@ -86,7 +86,8 @@ def load(path: str | None = None):
         L.hydro_get_time.argtypes = [_VP, _VP, _VP]
         L.hydro_upload.argtypes = [_VP, _VP, _SZ, _VP]
         L.hydro_download.argtypes = [_VP, _VP, _SZ, _VP]
-        L.hydro_debug_fields.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+        L.hydro_debug_fields.argtypes = [D, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]
         L.hydro_kernel_launches.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64)]
         L.hydro_profile_begin.argtypes = [_VP]
         L.hydro_profile_end.argtypes = [_VP, ctypes.POINTER(hydro_stage_time), i, ctypes.POINTER(i)]
@@ -164,10 +165,11 @@ def hydro_box_layout(descs, box: int) -> hydro_layout:
 
 
 def hydro_debug_fields(descs, box: int):
-    off, nf = ctypes.c_int64(), ctypes.c_int32()
+    """(byte offset in scratch, number of fields, element bytes) of box's intermediates."""
+    off, nf, eb = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().hydro_debug_fields(desc_array(descs), len(descs), int(box), ctypes.byref(off),
-                                     ctypes.byref(nf)))
-    return off.value, nf.value
+                                     ctypes.byref(nf), ctypes.byref(eb)))
+    return off.value, nf.value, eb.value
 
 
 def hydro_alloc(descs, state, state_bytes, scratch, scratch_bytes) -> int:
@@ -242,10 +244,10 @@ def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:
 class Boxes:
     """Owns torch-allocated state and scratch for a set of boxes and a handle."""
 
-    def __init__(self, problems_or_descs, device="cuda"):
+    def __init__(self, problems_or_descs, device="cuda", precision=HYDRO_FP64):
         import torch
         items = list(problems_or_descs)
-        self.descs = [p if isinstance(p, hydro_box_desc) else desc_of(p) for p in items]
+        self.descs = [p if isinstance(p, hydro_box_desc) else desc_of(p, precision) for p in items]
         self.nboxes = len(self.descs)
         sb, wb = hydro_workspace_size(self.descs)
         self.state_bytes, self.scratch_bytes = sb, wb
@@ -283,14 +285,17 @@ class Boxes:
                                 (lay.var_stride, lay.plane, lay.pitch, 1), lay.offset)
 
     def field_view(self, b, first, count=1):
-        """Diagnostic view of `count` scratch fields of box b starting at field `first`."""
+        """Diagnostic view of `count` scratch fields of box b starting at field `first`
+        (float64 for FP64 boxes, float32 for mixed-precision boxes)."""
         import torch
-        off, nf = hydro_debug_fields(self.descs, b)
+        off, nf, eb = hydro_debug_fields(self.descs, b)
         lay = self.layouts[b]
         nx, ny, nz = self.shape(b)
         g = HYDRO_NG
-        return torch.as_strided(self.scratch, (count, nz + 2 * g, ny + 2 * g, nx + 2 * g),
-                                (lay.var_stride, lay.plane, lay.pitch, 1), off + first * lay.var_stride)
+        base = self.scratch.view(torch.float32) if eb == 4 else self.scratch
+        assert off % eb == 0
+        return torch.as_strided(base, (count, nz + 2 * g, ny + 2 * g, nx + 2 * g),
+                                (lay.var_stride, lay.plane, lay.pitch, 1), off // eb + first * lay.var_stride)
 
     def set_interior(self, b, U):
         import torch

@@ -47,9 +47,15 @@ def test_workspace_and_layout_planning():
     assert lay.plane == 28 * 20
     assert lay.var_stride >= lay.plane * 17 and lay.var_stride % 32 == 0
     assert sb == 5 * lay.var_stride * 8
-    off, nf = hydro.hydro_debug_fields([d], 0)
-    assert nf == 112
-    assert wb >= (off + nf * lay.var_stride) * 8
+    off, nf, eb = hydro.hydro_debug_fields([d], 0)
+    assert nf == 112 and eb == 8 and off % 256 == 0
+    assert wb >= off + nf * lay.var_stride * 8
+    # a mixed-precision box keeps FP32 fields: half the scratch bytes
+    dm = hydro.desc_of(pr, hydro.HYDRO_MIXED)
+    sbm, wbm = hydro.hydro_workspace_size([dm])
+    offm, nfm, ebm = hydro.hydro_debug_fields([dm], 0)
+    assert sbm == sb and ebm == 4 and wbm >= offm + nfm * lay.var_stride * 4
+    assert wbm - offm < (wb - off) * 0.55
     # two boxes: the second starts right after the first
     d2 = hydro.desc_of(inputs.sod((32, 4, 4)))
     l2 = hydro.hydro_box_layout([d, d2], 1)
@@ -63,6 +69,7 @@ def test_workspace_and_layout_planning():
     ("cfl", 0.0, "cfl"),
     ("dx", -1.0, "widths"),
     ("precision", 7, "precision"),
+    ("precision", -1, "precision"),
 ])
 def test_invalid_descriptors_are_rejected(field, value, msg):
     d = hydro.desc_of(inputs.uniform(8))

@@ -120,7 +120,20 @@ def test_reflecting_walls_conserve_mass_energy_and_tangential_momentum():
     U0 = pr.U
     U, *_ = oracle.run(pr, nsteps=8, nthreads=NT)
     for v in (0, 1, 3, 4):
-        assert abs(U[v].sum() - U0[v].sum()) <= 1e-13 * np.abs(U0[v]).sum() * 3
+        assert abs(U[v].sum() - U0[v].sum()) <= 1e-13 * np.sqrt(8) * np.abs(U0[v]).sum()
+
+
+def test_reflecting_wall_fluxes_are_impermeable():
+    pr = inputs.kelvin_helmholtz((8, 10, 6), seed=3)
+    box = oracle.box_of(pr)
+    Ug = oracle.embed(pr.U)
+    oracle.fill_ghosts(box, Ug)
+    rc, W = oracle.step(box, Ug, oracle.compute_dt(box, Ug), dump=True)
+    g, ny = 4, 10
+    for wall in (g, g + ny):  # y faces at j = 0 and j = ny
+        F = W[oracle.W_F + 5 * 1:oracle.W_F + 5 * 2, g:-g, wall, g:-g]
+        assert np.all(F[[0, 1, 3, 4]] == 0.0)
+        assert np.all(F[2] > 0.0)  # the wall pressure
 
 
 def test_shear_layer_mirror_symmetry_about_midplane():
