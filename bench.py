@@ -186,6 +186,43 @@ def run_reference(args, rank: int) -> None:
     }), flush=True)
 
 
+# ------------------------------------------------------- batched uneven boxes
+def run_batched(hydro, inputs, torch, np, stream, nboxes=512, nsteps=30):
+    """512 independent Sedov boxes with edges drawn from {16,24,32,48,64}, 30
+    steps in one handle (one launch per stage over all boxes, one CUDA graph
+    per step), launch shapes autotuned first; FP64 and mixed precision."""
+    probs = inputs.sedov_batch(nboxes, seed=0, nsteps=nsteps)
+    zones = sum(p.zones for p in probs)
+    out = {"workload": f"sedov_batch_{nboxes}", "boxes": nboxes, "zones": zones, "steps": nsteps}
+    finals = {}
+    for name, prec in (("fp64", hydro.HYDRO_FP64), ("mixed", hydro.HYDRO_MIXED)):
+        B = hydro.Boxes(probs, precision=prec)
+        tuned = hydro.hydro_autotune(B.h, reps=2, stream=stream)
+        B.step(1)  # captures the step graph
+        B.sync()
+        for k, p in enumerate(probs):
+            B.set_interior(k, p.U)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hydro.hydro_step(B.h, None, nsteps, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        B.sync()
+        ms = e0.elapsed_time(e1)
+        finals[name] = [B.interior(k)[[0, 4]] for k in range(nboxes)]
+        B.close()
+        del B
+        out[name] = {"value": zones * nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / nsteps,
+                     "tuned": {f"{t[0]}{'' if t[1] == 0 else '_mixed'}": [t[2], t[3]] for t in tuned}}
+    worst = {n: max(float(np.abs(finals["mixed"][k][i] - finals["fp64"][k][i]).sum()
+                          / np.abs(finals["fp64"][k][i]).sum()) for k in range(nboxes))
+             for n, i in (("rho", 0), ("E", 1))}
+    out["mixed"]["worst_box_rel_l1_vs_fp64"] = worst
+    return out
+
+
 # ------------------------------------------------------------------ main arm
 def main() -> None:
     ap = argparse.ArgumentParser()
@@ -194,6 +231,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-box batched measurement")
     ap.add_argument("--box", type=int, default=N_BOX, help="box edge (default 256; smaller only for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -305,6 +343,7 @@ def main() -> None:
     del M
     rel_l1 = {name: float(np.abs(mixed_final[v] - fp64_final[v]).sum() / np.abs(fp64_final[v]).sum())
               for name, v in (("rho", 0), ("E", 4))}
+    batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
     mixed = {"value": world * N * args.steps / (ms_mixed * 1e-3), "unit": UNIT,
              "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
              "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
@@ -351,6 +390,7 @@ def main() -> None:
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "batched": batched,
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -161,8 +161,33 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset_bytes, int32_t* nfields,
                        int32_t* elem_bytes);
 
+/* Launch configuration.  Every stage kernel covers all boxes of the handle in
+ * one launch: the boxes' blocks are packed back to back through a work table
+ * in the scratch head (block -> box and axis), so uneven boxes waste no
+ * blocks.  hydro_step replays one step as a CUDA graph (captured on first use
+ * for a given dt_dev, on a private stream) unless profiling is on or graphs
+ * are switched off with hydro_use_graphs(h, 0).
+ *
+ * hydro_autotune times, for every stage kernel but the update and for each
+ * compute type present, threads per block in {64, 128, 256} and two box
+ * orders (as given, or largest work item first), `reps` launches each, keeps
+ * the fastest and writes one record per tuned table (up to max_entries;
+ * *nentries receives the count).  It does not change the state or the
+ * simulated time (it refills ghosts and recomputes intermediates only), and
+ * synchronises `stream` before returning. */
+typedef struct hydro_tuning {
+  char name[24];      /* fill_x, fill_y, fill_z, prim, flatten, slopes, trace, riemann, ctu1, ctu2 */
+  int32_t precision;  /* HYDRO_FP64 or HYDRO_MIXED kernels */
+  int32_t threads;    /* chosen threads per block */
+  int32_t order;      /* 0: boxes in the given order, 1: largest work item first */
+  float ms;           /* time of one launch with that choice */
+} hydro_tuning;
+int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries, int* nentries, void* stream);
+int hydro_use_graphs(hydro_handle* h, int enable);
+
 /* Number of kernels this handle has launched since hydro_alloc (a ghost fill
- * is three kernels, every other stage one), into *count. */
+ * is three kernels, every other stage one per compute type present), into
+ * *count. */
 int hydro_kernel_launches(hydro_handle* h, int64_t* count);
 
 /* Per-stage device time.  Between hydro_profile_begin and hydro_profile_end

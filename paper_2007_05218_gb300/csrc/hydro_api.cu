@@ -24,6 +24,12 @@ struct hydro_handle {
   std::vector<cudaEvent_t> events;   // event pool (pairs), reused across sessions
   std::vector<int> rec_stage;        // stage of each recorded pair
   std::vector<int> rec_kernels;      // kernels launched inside each recorded pair
+  // one step captured as a CUDA graph and replayed by hydro_step
+  bool use_graphs = true;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_dt = nullptr;  // dt_dev the graph was captured with
+  int graph_kernels = 0;
 };
 
 namespace {
@@ -68,7 +74,8 @@ int validate(const hydro_box_desc& d, int i) {
 struct Geometry {
   std::vector<HostBox> boxes;
   size_t state_elems = 0;
-  size_t table_bytes = 0, rt_bytes = 0, head_bytes = 0;
+  size_t table_bytes = 0, rt_bytes = 0, worktab_bytes = 0, head_bytes = 0;
+  int cap[hydro::NTABLES][2] = {};  // work-table capacities (items)
   size_t work_bytes = 0, stage_elems = 0;
   size_t scratch_bytes = 0;
 };
@@ -100,7 +107,22 @@ int plan_geometry(const hydro_box_desc* d, int nboxes, Geometry* g) {
   g->stage_elems = (size_t)stoff;
   g->table_bytes = align_up(sizeof(DevBox) * nboxes, ALIGN);
   g->rt_bytes = align_up(sizeof(BoxRt) * nboxes, ALIGN);
-  g->head_bytes = g->table_bytes + g->rt_bytes;
+  int nmixed = 0;
+  for (int i = 0; i < nboxes; i++) nmixed += d[i].precision == HYDRO_MIXED;
+  size_t ints = 0;
+  for (int t = 0; t < hydro::NTABLES; t++) {
+    if (hydro::TABLE_PER_PRECISION[t]) {
+      g->cap[t][0] = (nboxes - nmixed) * hydro::TABLE_ZDIM[t];
+      g->cap[t][1] = nmixed * hydro::TABLE_ZDIM[t];
+    } else {
+      g->cap[t][0] = nboxes * hydro::TABLE_ZDIM[t];
+      g->cap[t][1] = 0;
+    }
+    for (int s = 0; s < 2; s++)
+      if (g->cap[t][s]) ints += 2 * (size_t)g->cap[t][s] + 1;
+  }
+  g->worktab_bytes = align_up(ints * sizeof(int), ALIGN);
+  g->head_bytes = g->table_bytes + g->rt_bytes + g->worktab_bytes;
   // the field area doubles as the staging buffer of hydro_upload/download
   g->scratch_bytes = g->head_bytes + std::max(g->work_bytes, g->stage_elems * sizeof(double));
   return HYDRO_OK;
@@ -115,6 +137,27 @@ int check_device(const hydro_handle* h) {
 }
 
 int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? HYDRO_OK : cuda_fail(e, what); }
+
+void drop_graph(hydro_handle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_dt = nullptr;
+  h->graph_kernels = 0;
+}
+
+// Rebuilds one work table from its threads-per-block and order settings and
+// copies it to the device (synchronously).
+cudaError_t upload_table(hydro_handle* h, int t, int s) {
+  hydro::WorkTable& w = h->plan.tab[t][s];
+  if (w.capacity == 0) return cudaSuccess;
+  std::vector<int> start(w.capacity + 1), item(w.capacity);
+  w.nitems = hydro::build_table(h->plan, t, s, w.tpb, w.order, start.data(), item.data());
+  w.blocks = start[w.nitems];
+  cudaError_t e = cudaMemcpy(w.start, start.data(), sizeof(int) * (w.nitems + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w.item, item.data(), sizeof(int) * w.nitems, cudaMemcpyHostToDevice);
+  drop_graph(h);
+  return e;
+}
 
 // Launches one stage, bracketed by timing events when profiling is on.
 cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const double* dt_in = nullptr,
@@ -150,6 +193,46 @@ cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const do
 namespace hydro {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace hydro
+
+namespace {
+
+// The kernels of one step, in order, on stream s.
+cudaError_t launch_step(hydro_handle* h, const double* dt_dev, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int st = hydro::ST_FILL; st < hydro::NSTAGES && e == cudaSuccess; st++) {
+    if (st == hydro::ST_DT) e = run_stage(h, hydro::ST_DT, s, dt_dev, nullptr, 1);
+    else e = run_stage(h, static_cast<hydro::Stage>(st), s);
+  }
+  return e;
+}
+
+// Captures one step (for this dt_dev) into a CUDA graph on a private stream.
+int ensure_graph(hydro_handle* h, const double* dt_dev) {
+  if (h->graph && h->graph_dt == dt_dev) return HYDRO_OK;
+  drop_graph(h);
+  cudaError_t e = cudaSuccess;
+  if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "graph stream");
+  const long long before = h->launches;
+  e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+  cudaError_t le = launch_step(h, dt_dev, h->capture_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->capture_stream, &graph);
+  h->graph_kernels = (int)(h->launches - before);
+  h->launches = before;
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return cuda_fail(e, "capturing the step graph");
+  }
+  h->graph_dt = dt_dev;
+  return HYDRO_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -220,6 +303,25 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
   p.boxes = h->boxes.data();
   p.dboxes = reinterpret_cast<DevBox*>(scratch);
   p.rt = reinterpret_cast<BoxRt*>(scratch + g.table_bytes);
+  {
+    int* ip = reinterpret_cast<int*>(scratch + g.table_bytes + g.rt_bytes);
+    for (int t = 0; t < hydro::NTABLES; t++)
+      for (int s = 0; s < 2; s++) {
+        hydro::WorkTable& w = p.tab[t][s];
+        w.capacity = g.cap[t][s];
+        w.nitems = 0;
+        w.blocks = 0;
+        w.tpb = hydro::default_tpb(t);
+        w.order = 0;
+        w.start = w.item = nullptr;
+        if (w.capacity) {
+          w.start = ip;
+          ip += w.capacity + 1;
+          w.item = ip;
+          ip += w.capacity;
+        }
+      }
+  }
   p.state = static_cast<double*>(state_dev);
   p.work = reinterpret_cast<unsigned char*>(scratch + g.head_bytes);
   p.work_bytes = g.work_bytes;
@@ -262,6 +364,8 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
   }
   e = cudaMemcpy(p.dboxes, table.data(), sizeof(DevBox) * nboxes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p.rt, 0, sizeof(BoxRt) * nboxes);
+  for (int t = 0; t < hydro::NTABLES && e == cudaSuccess; t++)
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) e = upload_table(h, t, s);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     delete h;
@@ -274,6 +378,8 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
 int hydro_free(hydro_handle* h) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  drop_graph(h);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   delete h;
   return HYDRO_OK;
 }
@@ -301,12 +407,19 @@ int hydro_step(hydro_handle* h, const double* dt_dev, int nsteps, void* stream) 
   int rc = check_device(h);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (int i = 0; i < nsteps; i++) {
-    cudaError_t e = cudaSuccess;
-    for (int st = hydro::ST_FILL; st < hydro::NSTAGES && e == cudaSuccess; st++) {
-      if (st == hydro::ST_DT) e = run_stage(h, hydro::ST_DT, s, dt_dev, nullptr, 1);
-      else e = run_stage(h, static_cast<hydro::Stage>(st), s);
+  if (nsteps == 0) return HYDRO_OK;
+  if (h->use_graphs && !h->profiling) {
+    rc = ensure_graph(h, dt_dev);
+    if (rc) return rc;
+    for (int i = 0; i < nsteps; i++) {
+      cudaError_t e = cudaGraphLaunch(h->graph, s);
+      if (e != cudaSuccess) return cuda_fail(e, "step graph launch");
+      h->launches += h->graph_kernels;
     }
+    return HYDRO_OK;
+  }
+  for (int i = 0; i < nsteps; i++) {
+    cudaError_t e = launch_step(h, dt_dev, s);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
   }
   return HYDRO_OK;
@@ -383,6 +496,88 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
   if (e == cudaSuccess) e = cudaMemcpyAsync(state_host, stage, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return launched(e, "hydro_download");
+}
+
+int hydro_use_graphs(hydro_handle* h, int enable) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  h->use_graphs = enable != 0;
+  if (!h->use_graphs) drop_graph(h);
+  return HYDRO_OK;
+}
+
+int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries, int* nentries, void* stream) {
+  if (!h || !nentries || (max_entries > 0 && !out)) return fail(HYDRO_ERR_INVALID, "null argument");
+  if (reps < 1) return fail(HYDRO_ERR_INVALID, "reps must be >= 1");
+  int rc = check_device(h);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hydro::Plan& p = h->plan;
+  // scratch in a consistent state for the current interior, time not advanced
+  cudaError_t e = run_stage(h, hydro::ST_FILL, s);
+  if (e == cudaSuccess) e = run_stage(h, hydro::ST_PRIM, s);
+  if (e == cudaSuccess) e = run_stage(h, hydro::ST_DT, s, nullptr, nullptr, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_autotune: first pass");
+  cudaEvent_t ev[2];
+  e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_autotune: events");
+  const int tpbs[3] = {64, 128, 256};
+  int n = 0;
+  // pipeline order, so that every table is tuned on valid inputs
+  const int order[] = {hydro::TB_FILL_X, hydro::TB_FILL_Y, hydro::TB_FILL_Z, hydro::TB_PRIM, hydro::TB_FLATTEN,
+                       hydro::TB_SLOPES, hydro::TB_TRACE, hydro::TB_RIEMANN, hydro::TB_CTU1, hydro::TB_CTU2};
+  for (int t : order) {
+    for (int sl = 0; sl < 2; sl++) {
+      hydro::WorkTable& w = p.tab[t][sl];
+      if (w.capacity == 0) continue;
+      int best_tpb = w.tpb, best_order = w.order;
+      float best_ms = 0.f;
+      bool first = true;
+      for (int ti = 0; ti < 3 && e == cudaSuccess; ti++)
+        for (int o = 0; o < 2 && e == cudaSuccess; o++) {
+          w.tpb = tpbs[ti];
+          w.order = o;
+          e = upload_table(h, t, sl);
+          if (e == cudaSuccess) e = hydro::launch_table(p, t, sl, s);  // warm
+          if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+          for (int r = 0; r < reps && e == cudaSuccess; r++) e = hydro::launch_table(p, t, sl, s);
+          if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+          ms /= reps;
+          if (e == cudaSuccess && (first || ms < best_ms)) {
+            best_ms = ms;
+            best_tpb = w.tpb;
+            best_order = w.order;
+            first = false;
+          }
+        }
+      if (e != cudaSuccess) break;
+      w.tpb = best_tpb;
+      w.order = best_order;
+      e = upload_table(h, t, sl);
+      if (e == cudaSuccess) e = hydro::launch_table(p, t, sl, s);  // valid outputs for the next table
+      if (n < max_entries) {
+        memset(&out[n], 0, sizeof out[n]);
+        snprintf(out[n].name, sizeof out[n].name, "%s", hydro::TABLE_NAMES[t]);
+        out[n].precision = hydro::TABLE_PER_PRECISION[t] && sl == 1 ? HYDRO_MIXED : HYDRO_FP64;
+        out[n].threads = best_tpb;
+        out[n].order = best_order;
+        out[n].ms = best_ms;
+      }
+      n++;
+    }
+    if (e != cudaSuccess) break;
+  }
+  // the tuning launches of k_prim left their maxima behind: reset them
+  if (e == cudaSuccess) e = run_stage(h, hydro::ST_DT, s, nullptr, nullptr, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_autotune");
+  *nentries = n;
+  return HYDRO_OK;
 }
 
 int hydro_kernel_launches(hydro_handle* h, int64_t* count) {

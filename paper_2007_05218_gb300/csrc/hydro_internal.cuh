@@ -78,6 +78,38 @@ struct HostBox {
   long long interior;  // nx*ny*nz
 };
 
+// Work tables: every launch of a stage covers a list of work items (one box,
+// or one box and axis / axis pair) whose blocks are packed back to back, so
+// boxes of uneven size waste no blocks.  Block b of a launch belongs to the
+// item i with start[i] <= b < start[i+1]; item[i] = box * 8 + axis (or pair).
+enum TableId : int {
+  TB_FILL_X = 0,
+  TB_FILL_Y,
+  TB_FILL_Z,
+  TB_PRIM,
+  TB_UPDATE,
+  TB_FLATTEN,
+  TB_SLOPES,
+  TB_TRACE,
+  TB_RIEMANN,
+  TB_CTU1,
+  TB_CTU2,
+  NTABLES
+};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 6, 3};
+// tables of the precision-specific stage kernels exist once per compute type
+constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true};
+
+struct WorkTable {
+  int* start;      // device, nitems + 1 entries (start[nitems] = blocks)
+  int* item;       // device, nitems entries
+  int nitems;      // 0: nothing to launch
+  int capacity;    // items the device arrays hold
+  int blocks;      // blocks of one launch
+  int tpb;         // threads per block
+  int order;       // 0: box order, 1: largest items first
+};
+
 // Host-side plan of a handle.
 struct Plan {
   int nboxes;
@@ -90,7 +122,16 @@ struct Plan {
   bool has_fp64, has_mixed;
   int max_n[3];        // max interior extent per axis over boxes
   long long max_ghosted, max_interior;
+  WorkTable tab[NTABLES][2];  // [table][0: FP64 boxes (or all boxes), 1: mixed boxes]
 };
+
+// Threads per block each table starts with (before any autotuning).
+int default_tpb(int table);
+// Cells (threads) of work item (box, z) of a table.
+long long item_volume(const hydro_box_desc& d, int table, int z);
+// Fills the host copies of a table for the given precision slot, threads per
+// block and order; returns the number of items.
+int build_table(const Plan& p, int table, int slot, int tpb, int order, int* start, int* item);
 
 // Stages of one step, in launch order.  Each stage is one kernel, except the
 // ghost fill (three kernels: x, y, z).
@@ -115,6 +156,10 @@ extern const char* const STAGE_NAMES[NSTAGES];
 // when dt_out is not null, and advances the per-box time when `advance` is set.
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
                          int advance, int* launched);
+// Launches the kernel of one work table for one precision slot (every table
+// but TB_UPDATE; used by the autotuner, which must not change the state).
+cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream);
+extern const char* const TABLE_NAMES[NTABLES];
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream);
 // Sets the thread-local message returned by hydro_last_error (hydro_api.cu).
 void set_last_error(const std::string& msg);

@@ -29,14 +29,13 @@
 //   k_update     conservative flux-divergence update (FP64) + physicality flag
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fp64_fast.cuh"
 #include "hydro_internal.cuh"
 
 namespace hydro {
 namespace {
-
-constexpr int TPB = 128;
 
 // slot m of the normal frame of axis D -> x,y,z component (0 rho, 1..3 velocity/momentum, 4 p/E)
 template <int D>
@@ -72,12 +71,39 @@ __device__ __forceinline__ bool decode(long long t, const int* lo, const int* ex
   return true;
 }
 
-__device__ __forceinline__ long long tid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+// Device view of a work table: block -> (box, axis) and the thread's index in
+// the item's region (binary search over the item start blocks).
+struct TableView {
+  const int* start;
+  const int* item;
+  int nitems;
+};
+
+__device__ __forceinline__ int locate(const TableView& w, int* z, long long* t) {
+  const int blk = blockIdx.x;
+  int lo = 0, hi = w.nitems;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(w.start + mid) <= blk) lo = mid;
+    else hi = mid;
+  }
+  const int code = __ldg(w.item + lo);
+  *z = code & 7;
+  *t = (long long)(blk - __ldg(w.start + lo)) * blockDim.x + threadIdx.x;
+  return code >> 3;
+}
+
+#define LOCATE(tv)                  \
+  int z_;                           \
+  long long t_;                     \
+  const int bi = locate(tv, &z_, &t_); \
+  const DevBox& b = boxes[bi];
 
 // ----------------------------------------------------------------- ghost fill
 template <int D>
-__global__ void __launch_bounds__(256) k_fill(const DevBox* __restrict__ boxes, double* __restrict__ state) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __restrict__ boxes,
+                                              double* __restrict__ state) {
+  LOCATE(tv)
   int lo[3], ext[3], c[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -85,7 +111,7 @@ __global__ void __launch_bounds__(256) k_fill(const DevBox* __restrict__ boxes, 
     else if (a < D) { lo[a] = -NG; ext[a] = b.n[a] + 2 * NG; }
     else { lo[a] = 0; ext[a] = b.n[a]; }
   }
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const int l = c[D], n = b.n[D];
   const int side = l < NG ? 0 : 1;
   const int m = side == 0 ? NG - l : l - NG + 1;  // depth 1..NG
@@ -110,15 +136,15 @@ __global__ void __launch_bounds__(256) k_fill(const DevBox* __restrict__ boxes, 
 // ------------------------------------------------- conserved -> primitive, dt
 // FP64 arithmetic for every box (the dt reduction needs it); the primitive
 // fields are stored in the box's compute type.
-__global__ void __launch_bounds__(256) k_prim(const DevBox* __restrict__ boxes, const double* __restrict__ state,
-                                              unsigned char* __restrict__ work, BoxRt* __restrict__ rt) {
-  const int bi = blockIdx.y;
-  const DevBox& b = boxes[bi];
+__global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes,
+                                              const double* __restrict__ state, unsigned char* __restrict__ work,
+                                              BoxRt* __restrict__ rt) {
+  LOCATE(tv)
   int lo[3] = {-NG, -NG, -NG};
   int ext[3] = {b.n[0] + 2 * NG, b.n[1] + 2 * NG, b.n[2] + 2 * NG};
   int c[3];
   unsigned long long sbits = 0ull;
-  if (decode(tid(), lo, ext, c)) {
+  if (decode(t_, lo, ext, c)) {
     const long long Z = zone(b, c[0], c[1], c[2]);
     const long long vs = b.vs;
     const double* U = state + b.state_off;
@@ -187,11 +213,12 @@ __device__ __forceinline__ R flat_tilde(const R* __restrict__ p, const R* __rest
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_flatten(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_flatten(TableView tv, const DevBox* __restrict__ boxes,
+                                                 unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   const R* p = W + 4 * b.vs;
@@ -233,14 +260,15 @@ __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_slopes(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __restrict__ boxes,
+                                                unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
-  const int d = blockIdx.z;
+  const int d = z_;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   lo[d] = -2;
   ext[d] = b.n[d] + 4;
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   switch (d) {
@@ -375,16 +403,16 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_trace(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                               unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __restrict__ boxes,
+                                               const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[blockIdx.y].dt;
-  switch (blockIdx.z) {
+  const double dt = rt[bi].dt;
+  switch (z_) {
     case 0: trace_zone<R, 0>(b, W, Z, R(dt * b.idx[0])); break;
     case 1: trace_zone<R, 1>(b, W, Z, R(dt * b.idx[1])); break;
     default: trace_zone<R, 2>(b, W, Z, R(dt * b.idx[2])); break;
@@ -480,14 +508,15 @@ __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_riemann(const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __restrict__ boxes,
+                                                 unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
-  const int d = blockIdx.z;
+  const int d = z_;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   lo[d] = 0;
   ext[d] = b.n[d] + 1;
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   switch (d) {
@@ -548,11 +577,11 @@ __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, lo
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_ctu1(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                              unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __restrict__ boxes,
+                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
-  const int p = blockIdx.z;  // pair slot: xy xz yx yz zx zy
+  const int p = z_;  // pair slot: xy xz yx yz zx zy
   const int d = p / 2, r = p % 2;
   const int e = r == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);
   const int f = 3 - d - e;
@@ -560,10 +589,10 @@ __global__ void __launch_bounds__(TPB) k_ctu1(const DevBox* __restrict__ boxes, 
   lo[d] = 0; ext[d] = b.n[d] + 1;
   lo[e] = 0; ext[e] = b.n[e];
   lo[f] = -1; ext[f] = b.n[f] + 2;
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[blockIdx.y].dt;
+  const double dt = rt[bi].dt;
   switch (p) {
     case 0: ctu1_face<R, 0, 1>(b, W, Z, dt); break;
     case 1: ctu1_face<R, 0, 2>(b, W, Z, dt); break;
@@ -598,17 +627,17 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB) k_ctu2(const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt,
-                                              unsigned char* __restrict__ work) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __restrict__ boxes,
+                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
   if (!box_uses<R>(b)) return;
-  const int d = blockIdx.z;
+  const int d = z_;
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
   ext[d] = b.n[d] + 1;
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[blockIdx.y].dt;
+  const double dt = rt[bi].dt;
   const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT) ||
                     (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT);
   switch (d) {
@@ -638,12 +667,12 @@ __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256) k_update(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt,
-                                                double* __restrict__ state, unsigned char* __restrict__ work) {
-  const int bi = blockIdx.y;
-  const DevBox& b = boxes[bi];
+__global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __restrict__ boxes,
+                                                BoxRt* __restrict__ rt, double* __restrict__ state,
+                                                unsigned char* __restrict__ work) {
+  LOCATE(tv)
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   double* U = state + b.state_off;
   const double dt = rt[bi].dt;
@@ -656,11 +685,11 @@ __global__ void __launch_bounds__(256) k_update(const DevBox* __restrict__ boxes
 }
 
 // ----------------------------------------------------- host staging transfers
-__global__ void __launch_bounds__(256) k_scatter(const DevBox* __restrict__ boxes, double* __restrict__ state,
-                                                 const double* __restrict__ stage) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_scatter(TableView tv, const DevBox* __restrict__ boxes,
+                                                 double* __restrict__ state, const double* __restrict__ stage) {
+  LOCATE(tv)
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   const long long N = (long long)b.n[0] * b.n[1] * b.n[2];
   const long long src = b.stage_off + ((long long)c[2] * b.n[1] + c[1]) * b.n[0] + c[0];
@@ -668,11 +697,11 @@ __global__ void __launch_bounds__(256) k_scatter(const DevBox* __restrict__ boxe
   for (int v = 0; v < 5; v++) state[b.state_off + v * b.vs + Z] = stage[src + v * N];
 }
 
-__global__ void __launch_bounds__(256) k_gather(const DevBox* __restrict__ boxes, const double* __restrict__ state,
-                                                double* __restrict__ stage) {
-  const DevBox& b = boxes[blockIdx.y];
+__global__ void __launch_bounds__(256) k_gather(TableView tv, const DevBox* __restrict__ boxes,
+                                                const double* __restrict__ state, double* __restrict__ stage) {
+  LOCATE(tv)
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
-  if (!decode(tid(), lo, ext, c)) return;
+  if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   const long long N = (long long)b.n[0] * b.n[1] * b.n[2];
   const long long dst = b.stage_off + ((long long)c[2] * b.n[1] + c[1]) * b.n[0] + c[0];
@@ -680,169 +709,189 @@ __global__ void __launch_bounds__(256) k_gather(const DevBox* __restrict__ boxes
   for (int v = 0; v < 5; v++) stage[dst + v * N] = state[b.state_off + v * b.vs + Z];
 }
 
-// max over boxes of the volume of a region whose extent on axis a is n[a] + add[a]
-long long max_volume(const Plan& p, int a0, int a1, int a2) {
-  long long m = 0;
-  for (int i = 0; i < p.nboxes; i++) {
-    const hydro_box_desc& d = p.boxes[i].d;
-    long long v = (long long)(d.nx + a0) * (d.ny + a1) * (d.nz + a2);
-    if (v > m) m = v;
-  }
-  return m;
-}
-
-// max over boxes and axis orders of a face region: axis a has n+1 faces,
-// axis e is interior, axis f has n + fext zones (fext = 2 for CTU stage 1, 0 for stage 2)
-long long max_volume_faces(const Plan& p, int fext) {
-  long long m = 0;
-  for (int i = 0; i < p.nboxes; i++) {
-    const hydro_box_desc& d = p.boxes[i].d;
-    const int n[3] = {d.nx, d.ny, d.nz};
-    for (int a = 0; a < 3; a++)
-      for (int e = 0; e < 3; e++) {
-        if (e == a) continue;
-        const int f = 3 - a - e;
-        const long long v = (long long)(n[a] + 1) * n[e] * (n[f] + fext);
-        if (v > m) m = v;
-      }
-  }
-  return m;
-}
-
-// max over boxes and axes of a region with axis a extended by `along` and the
-// two other axes by `across`
-long long max_volume_axis(const Plan& p, int along, int across) {
-  long long m = 0;
-  for (int i = 0; i < p.nboxes; i++) {
-    const hydro_box_desc& d = p.boxes[i].d;
-    const int n[3] = {d.nx, d.ny, d.nz};
-    for (int a = 0; a < 3; a++)
-      m = std::max(m, (long long)(n[a] + along) * (n[(a + 1) % 3] + across) * (n[(a + 2) % 3] + across));
-  }
-  return m;
-}
-
-dim3 grid_for(long long vol, int tpb, int nboxes, int z = 1) {
-  long long bx = (vol + tpb - 1) / tpb;
-  if (bx < 1) bx = 1;
-  return dim3((unsigned)bx, (unsigned)nboxes, (unsigned)z);
-}
-
-// Launches the templated stage kernel for each compute type present in the plan.
-template <template <typename> class K>
-cudaError_t per_precision(const Plan& p, cudaStream_t s, int* launched) {
-  if (p.has_fp64) {
-    K<double>::go(p, s);
-    ++*launched;
-  }
-  if (p.has_mixed) {
-    K<float>::go(p, s);
-    ++*launched;
-  }
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "slopes", "trace",
                                            "riemann", "ctu1", "ctu2", "update"};
 
+const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
+                                           "slopes", "trace", "riemann", "ctu1", "ctu2"};
+
+int default_tpb(int table) {
+  switch (table) {
+    case TB_TRACE:
+    case TB_RIEMANN:
+    case TB_CTU1:
+    case TB_CTU2:
+    case TB_FLATTEN:
+      return 128;
+    default:
+      return 256;
+  }
+}
+
+// Threads of work item (box d, axis or pair z) of a table: the region the
+// matching kernel decodes.
+long long item_volume(const hydro_box_desc& d, int table, int z) {
+  const long long n[3] = {d.nx, d.ny, d.nz};
+  const long long g2 = 2 * NG;
+  switch (table) {
+    case TB_FILL_X: return g2 * n[1] * n[2];
+    case TB_FILL_Y: return (n[0] + g2) * g2 * n[2];
+    case TB_FILL_Z: return (n[0] + g2) * (n[1] + g2) * g2;
+    case TB_PRIM: return (n[0] + g2) * (n[1] + g2) * (n[2] + g2);
+    case TB_UPDATE: return n[0] * n[1] * n[2];
+    case TB_FLATTEN:
+    case TB_TRACE: return (n[0] + 2) * (n[1] + 2) * (n[2] + 2);
+    case TB_SLOPES: return (n[z] + 4) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
+    case TB_RIEMANN: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
+    case TB_CTU1: {
+      const int dd = z / 2, r = z % 2;
+      const int e = r == 0 ? (dd == 0 ? 1 : 0) : (dd == 2 ? 1 : 2);
+      const int f = 3 - dd - e;
+      return (n[dd] + 1) * n[e] * (n[f] + 2);
+    }
+    case TB_CTU2: return (n[z] + 1) * n[(z + 1) % 3] * n[(z + 2) % 3];
+    default: return 0;
+  }
+}
+
+int build_table(const Plan& p, int table, int slot, int tpb, int order, int* start, int* item) {
+  struct It {
+    int code;
+    int blocks;
+  };
+  std::vector<It> items;
+  for (int b = 0; b < p.nboxes; b++) {
+    const hydro_box_desc& d = p.boxes[b].d;
+    if (TABLE_PER_PRECISION[table] && (d.precision == HYDRO_MIXED) != (slot == 1)) continue;
+    for (int z = 0; z < TABLE_ZDIM[table]; z++) {
+      const long long v = item_volume(d, table, z);
+      items.push_back({b * 8 + z, (int)((v + tpb - 1) / tpb)});
+    }
+  }
+  if (order == 1)
+    std::stable_sort(items.begin(), items.end(), [](const It& a, const It& c) { return a.blocks > c.blocks; });
+  int acc = 0;
+  for (size_t i = 0; i < items.size(); i++) {
+    start[i] = acc;
+    item[i] = items[i].code;
+    acc += items[i].blocks;
+  }
+  start[items.size()] = acc;
+  return (int)items.size();
+}
+
 namespace {
-template <typename R>
-struct LFlatten {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_flatten<R><<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes), TPB, 0, s>>>(p.dboxes, p.work);
-  }
-};
-template <typename R>
-struct LSlopes {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_slopes<R><<<grid_for(max_volume_axis(p, 4, 2), 256, p.nboxes, 3), 256, 0, s>>>(p.dboxes, p.work);
-  }
-};
-template <typename R>
-struct LTrace {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_trace<R><<<grid_for(max_volume(p, 2, 2, 2), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
-  }
-};
-template <typename R>
-struct LRiemann {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_riemann<R><<<grid_for(max_volume_axis(p, 1, 2), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.work);
-  }
-};
-template <typename R>
-struct LCtu1 {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_ctu1<R><<<grid_for(max_volume_faces(p, 2), TPB, p.nboxes, 6), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
-  }
-};
-template <typename R>
-struct LCtu2 {
-  static void go(const Plan& p, cudaStream_t s) {
-    k_ctu2<R><<<grid_for(max_volume_faces(p, 0), TPB, p.nboxes, 3), TPB, 0, s>>>(p.dboxes, p.rt, p.work);
-  }
-};
+
+TableView view(const WorkTable& w) { return TableView{w.start, w.item, w.nitems}; }
+
+// Launches kernel `k` over table w, if it has work.
+template <typename... A, typename... P>
+int launch(void (*k)(TableView, A...), const WorkTable& w, cudaStream_t s, P... args) {
+  if (w.nitems == 0) return 0;
+  k<<<w.blocks, w.tpb, 0, s>>>(view(w), args...);
+  return 1;
+}
+
 }  // namespace
 
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
                          int advance, int* launched) {
   int n = 0;
-  cudaError_t e = cudaSuccess;
+  const auto& T = p.tab;
   switch (st) {
-    case ST_FILL: {
-      long long vx = 0, vy = 0, vz = 0;
-      for (int i = 0; i < p.nboxes; i++) {
-        const hydro_box_desc& d = p.boxes[i].d;
-        vx = std::max(vx, (long long)2 * NG * d.ny * d.nz);
-        vy = std::max(vy, (long long)2 * NG * (d.nx + 2 * NG) * d.nz);
-        vz = std::max(vz, (long long)2 * NG * (d.nx + 2 * NG) * (d.ny + 2 * NG));
-      }
-      k_fill<0><<<grid_for(vx, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
-      k_fill<1><<<grid_for(vy, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
-      k_fill<2><<<grid_for(vz, 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state);
-      n = 3;
-      e = cudaGetLastError();
+    case ST_FILL:
+      n += launch(k_fill<0>, T[TB_FILL_X][0], stream, p.dboxes, p.state);
+      n += launch(k_fill<1>, T[TB_FILL_Y][0], stream, p.dboxes, p.state);
+      n += launch(k_fill<2>, T[TB_FILL_Z][0], stream, p.dboxes, p.state);
       break;
-    }
     case ST_PRIM:
-      k_prim<<<grid_for(max_volume(p, 2 * NG, 2 * NG, 2 * NG), 256, p.nboxes), 256, 0, stream>>>(
-          p.dboxes, p.state, p.work, p.rt);
-      n = 1;
-      e = cudaGetLastError();
+      n += launch(k_prim, T[TB_PRIM][0], stream, p.dboxes, (const double*)p.state, p.work, p.rt);
       break;
     case ST_DT:
       k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
       n = 1;
-      e = cudaGetLastError();
       break;
-    case ST_FLATTEN: e = per_precision<LFlatten>(p, stream, &n); break;
-    case ST_SLOPES: e = per_precision<LSlopes>(p, stream, &n); break;
-    case ST_TRACE: e = per_precision<LTrace>(p, stream, &n); break;
-    case ST_RIEMANN: e = per_precision<LRiemann>(p, stream, &n); break;
-    case ST_CTU1: e = per_precision<LCtu1>(p, stream, &n); break;
-    case ST_CTU2: e = per_precision<LCtu2>(p, stream, &n); break;
+    case ST_FLATTEN:
+      n += launch(k_flatten<double>, T[TB_FLATTEN][0], stream, p.dboxes, p.work);
+      n += launch(k_flatten<float>, T[TB_FLATTEN][1], stream, p.dboxes, p.work);
+      break;
+    case ST_SLOPES:
+      n += launch(k_slopes<double>, T[TB_SLOPES][0], stream, p.dboxes, p.work);
+      n += launch(k_slopes<float>, T[TB_SLOPES][1], stream, p.dboxes, p.work);
+      break;
+    case ST_TRACE:
+      n += launch(k_trace<double>, T[TB_TRACE][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      n += launch(k_trace<float>, T[TB_TRACE][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      break;
+    case ST_RIEMANN:
+      n += launch(k_riemann<double>, T[TB_RIEMANN][0], stream, p.dboxes, p.work);
+      n += launch(k_riemann<float>, T[TB_RIEMANN][1], stream, p.dboxes, p.work);
+      break;
+    case ST_CTU1:
+      n += launch(k_ctu1<double>, T[TB_CTU1][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      n += launch(k_ctu1<float>, T[TB_CTU1][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      break;
+    case ST_CTU2:
+      n += launch(k_ctu2<double>, T[TB_CTU2][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      n += launch(k_ctu2<float>, T[TB_CTU2][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
+      break;
     case ST_UPDATE:
-      k_update<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.rt, p.state,
-                                                                                   p.work);
-      n = 1;
-      e = cudaGetLastError();
+      n += launch(k_update, T[TB_UPDATE][0], stream, p.dboxes, p.rt, p.state, p.work);
       break;
     default:
       return cudaErrorInvalidValue;
   }
   if (launched) *launched = n;
-  return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream) {
+  const WorkTable& w = p.tab[table][slot];
+  const BoxRt* rt = p.rt;
+  switch (table) {
+    case TB_FILL_X: launch(k_fill<0>, w, stream, p.dboxes, p.state); break;
+    case TB_FILL_Y: launch(k_fill<1>, w, stream, p.dboxes, p.state); break;
+    case TB_FILL_Z: launch(k_fill<2>, w, stream, p.dboxes, p.state); break;
+    case TB_PRIM: launch(k_prim, w, stream, p.dboxes, (const double*)p.state, p.work, p.rt); break;
+    case TB_FLATTEN:
+      if (slot == 0) launch(k_flatten<double>, w, stream, p.dboxes, p.work);
+      else launch(k_flatten<float>, w, stream, p.dboxes, p.work);
+      break;
+    case TB_SLOPES:
+      if (slot == 0) launch(k_slopes<double>, w, stream, p.dboxes, p.work);
+      else launch(k_slopes<float>, w, stream, p.dboxes, p.work);
+      break;
+    case TB_TRACE:
+      if (slot == 0) launch(k_trace<double>, w, stream, p.dboxes, rt, p.work);
+      else launch(k_trace<float>, w, stream, p.dboxes, rt, p.work);
+      break;
+    case TB_RIEMANN:
+      if (slot == 0) launch(k_riemann<double>, w, stream, p.dboxes, p.work);
+      else launch(k_riemann<float>, w, stream, p.dboxes, p.work);
+      break;
+    case TB_CTU1:
+      if (slot == 0) launch(k_ctu1<double>, w, stream, p.dboxes, rt, p.work);
+      else launch(k_ctu1<float>, w, stream, p.dboxes, rt, p.work);
+      break;
+    case TB_CTU2:
+      if (slot == 0) launch(k_ctu2<double>, w, stream, p.dboxes, rt, p.work);
+      else launch(k_ctu2<float>, w, stream, p.dboxes, rt, p.work);
+      break;
+    default:
+      return cudaErrorInvalidValue;  // the update changes the state and is not relaunched
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream) {
-  k_scatter<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state, stage);
+  launch(k_scatter, p.tab[TB_UPDATE][0], stream, p.dboxes, p.state, stage);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream) {
-  k_gather<<<grid_for(max_volume(p, 0, 0, 0), 256, p.nboxes), 256, 0, stream>>>(p.dboxes, p.state, stage);
+  launch(k_gather, p.tab[TB_UPDATE][0], stream, p.dboxes, (const double*)p.state, stage);
   return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ HYDRO_NG = 4
 EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_free", "hydro_fill_ghosts",
             "hydro_compute_dt", "hydro_step", "hydro_sync", "hydro_get_time", "hydro_upload",
             "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
-            "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_last_error")
+            "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
+            "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -51,6 +52,11 @@ class hydro_box_desc(ctypes.Structure):
 class hydro_layout(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_int64), ("pitch", ctypes.c_int64), ("plane", ctypes.c_int64),
                 ("var_stride", ctypes.c_int64)]
+
+
+class hydro_tuning(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("precision", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class hydro_stage_time(ctypes.Structure):
@@ -92,6 +98,8 @@ def load(path: str | None = None):
         L.hydro_profile_begin.argtypes = [_VP]
         L.hydro_profile_end.argtypes = [_VP, ctypes.POINTER(hydro_stage_time), i, ctypes.POINTER(i)]
         L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
+        L.hydro_autotune.argtypes = [_VP, i, ctypes.POINTER(hydro_tuning), i, ctypes.POINTER(i), _VP]
+        L.hydro_use_graphs.argtypes = [_VP, i]
         L.hydro_last_error.restype = ctypes.c_char_p
         L.hydro_last_error.argtypes = []
         _lib = L
@@ -231,6 +239,18 @@ def hydro_profile_end(h: int) -> dict:
     n = ctypes.c_int()
     _check(load().hydro_profile_end(h, buf, 32, ctypes.byref(n)))
     return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(n.value)}
+
+
+def hydro_autotune(h: int, reps: int = 3, stream=None) -> list:
+    """[(table, precision, threads, order, ms)] chosen per stage table."""
+    buf = (hydro_tuning * 64)()
+    n = ctypes.c_int()
+    _check(load().hydro_autotune(h, int(reps), buf, 64, ctypes.byref(n), _stream(stream)))
+    return [(buf[k].name.decode(), buf[k].precision, buf[k].threads, buf[k].order, buf[k].ms) for k in range(n.value)]
+
+
+def hydro_use_graphs(h: int, enable: bool) -> None:
+    _check(load().hydro_use_graphs(h, int(bool(enable))))
 
 
 def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:
