@@ -233,6 +233,59 @@ int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, in
 int hydro_compute_dt_noalloc(const hydro_box_desc* d, int nboxes, const double* state_dev, double* dt_dev,
                              void* stream);
 
+/* ---- served form: continuous batching of independent requests ----
+ * A server owns one scheduler thread and a caller-owned device pool (the
+ * memory budget).  hydro_submit copies a request (box, interior initial state,
+ * step count) and returns at once with a ticket.  The scheduler admits queued
+ * requests in submission order into up to max_active resident slots as slots
+ * and pool memory free up (a later, smaller request may pass a head that does
+ * not fit yet), uploads their states on a copy stream, and every tick advances
+ * all resident requests by one step with one launch per stage over all of
+ * them (each request keeps its own dt and precision).  Finished requests leave
+ * the batch at once; their results are copied back while the next tick
+ * computes.  A request's result does not depend on what else is resident: it
+ * is bitwise the same alone and in the mix.  hydro_poll returns HYDRO_PENDING
+ * until the result is on the host, then copies it out once.
+ *
+ * The pool holds the server's tables (a few hundred bytes per slot) and, per
+ * resident request, its ghosted FP64 state and its scratch fields; a request
+ * that could never fit the pool is refused with HYDRO_ERR_NOMEM at submit. */
+typedef struct hydro_server hydro_server;
+typedef struct hydro_server_config {
+  void* pool_dev;      /* device pool, 256-byte aligned; may be NULL with dry_run */
+  size_t pool_bytes;   /* budget: bytes of the pool */
+  int32_t max_active;  /* resident slots, 1..4096 */
+  int32_t dry_run;     /* 1: no GPU work (a tick completes one step of every resident
+                          request instantly and the result equals the initial state);
+                          for checks of the admission logic */
+} hydro_server_config;
+typedef struct hydro_request {
+  hydro_box_desc desc;    /* the box, its boundary conditions and precision */
+  const double* ic_host;  /* interior initial state [5][nz][ny][nx] (copied at submit) */
+  int32_t nsteps;         /* steps to advance (>= 0), dt from the state each step */
+} hydro_request;
+typedef struct hydro_result {
+  int32_t status;    /* HYDRO_OK, HYDRO_ERR_NONPHYSICAL, HYDRO_ERR_CUDA, ... */
+  int32_t steps;     /* steps taken */
+  double time;       /* simulated time reached */
+  double queued_s;   /* wall seconds from submit to admission */
+  double latency_s;  /* wall seconds from submit to the result on the host */
+} hydro_result;
+typedef struct hydro_server_stats {
+  int64_t queued, active, admitted, finished, ticks, kernel_launches;
+  int64_t bytes_in_use, peak_bytes, budget_bytes;
+} hydro_server_stats;
+int hydro_server_create(const hydro_server_config* cfg, hydro_server** out);
+/* Stops admitting (queued requests are cancelled with HYDRO_ERR_INVALID),
+ * finishes the resident ones, joins the scheduler and releases host state. */
+int hydro_server_destroy(hydro_server* s);
+int hydro_submit(hydro_server* s, const hydro_request* r, int64_t* ticket);
+/* HYDRO_PENDING while running; HYDRO_OK once done (copies the interior result,
+ * [5][nz][ny][nx] doubles, into out_host when it is not NULL; out_bytes must
+ * match) and forgets the ticket; a failed request returns its error code. */
+int hydro_poll(hydro_server* s, int64_t ticket, double* out_host, size_t out_bytes, hydro_result* info);
+int hydro_server_get_stats(hydro_server* s, hydro_server_stats* out);
+
 /* Thread-local description of the last error (never NULL). */
 const char* hydro_last_error(void);
 

@@ -76,6 +76,7 @@ struct HostBox {
   long long pitch, plane, vs;
   long long state_off, work_off, stage_off;  // work_off in bytes
   long long interior;  // nx*ny*nz
+  bool active = true;  // false: a free slot of a server plan (no work items)
 };
 
 // Work tables: every launch of a stage covers a list of work items (one box,

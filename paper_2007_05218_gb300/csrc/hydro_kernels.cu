@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
 __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, int nboxes,
                      const double* __restrict__ dt_in, double* __restrict__ dt_out, int advance) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nboxes; b += gridDim.x * blockDim.x) {
+    if (boxes[b].n[0] == 0) continue;  // a free slot of a server plan
     const double smax = __longlong_as_double((long long)rt[b].smax);
     const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
     rt[b].smax = 0ull;
@@ -763,6 +764,7 @@ int build_table(const Plan& p, int table, int slot, int tpb, int order, int* sta
   };
   std::vector<It> items;
   for (int b = 0; b < p.nboxes; b++) {
+    if (!p.boxes[b].active) continue;
     const hydro_box_desc& d = p.boxes[b].d;
     if (TABLE_PER_PRECISION[table] && (d.precision == HYDRO_MIXED) != (slot == 1)) continue;
     for (int z = 0; z < TABLE_ZDIM[table]; z++) {

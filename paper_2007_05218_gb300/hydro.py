@@ -33,7 +33,8 @@ EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_fr
             "hydro_compute_dt", "hydro_step", "hydro_sync", "hydro_get_time", "hydro_upload",
             "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
             "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
-            "hydro_last_error")
+            "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
+            "hydro_server_get_stats", "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -57,6 +58,25 @@ class hydro_layout(ctypes.Structure):
 class hydro_tuning(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("precision", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class hydro_server_config(ctypes.Structure):
+    _fields_ = [("pool_dev", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("dry_run", ctypes.c_int32)]
+
+
+class hydro_request(ctypes.Structure):
+    _fields_ = [("desc", hydro_box_desc), ("ic_host", ctypes.c_void_p), ("nsteps", ctypes.c_int32)]
+
+
+class hydro_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("time", ctypes.c_double),
+                ("queued_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+
+class hydro_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("queued", "active", "admitted", "finished", "ticks",
+                                              "kernel_launches", "bytes_in_use", "peak_bytes", "budget_bytes")]
 
 
 class hydro_stage_time(ctypes.Structure):
@@ -100,6 +120,11 @@ def load(path: str | None = None):
         L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
         L.hydro_autotune.argtypes = [_VP, i, ctypes.POINTER(hydro_tuning), i, ctypes.POINTER(i), _VP]
         L.hydro_use_graphs.argtypes = [_VP, i]
+        L.hydro_server_create.argtypes = [ctypes.POINTER(hydro_server_config), ctypes.POINTER(_VP)]
+        L.hydro_server_destroy.argtypes = [_VP]
+        L.hydro_submit.argtypes = [_VP, ctypes.POINTER(hydro_request), ctypes.POINTER(ctypes.c_int64)]
+        L.hydro_poll.argtypes = [_VP, ctypes.c_int64, _VP, _SZ, ctypes.POINTER(hydro_result)]
+        L.hydro_server_get_stats.argtypes = [_VP, ctypes.POINTER(hydro_server_stats)]
         L.hydro_last_error.restype = ctypes.c_char_p
         L.hydro_last_error.argtypes = []
         _lib = L
@@ -258,6 +283,84 @@ def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:
     without a handle or caller scratch (the library's static scratch is used)."""
     _check(load().hydro_compute_dt_noalloc(desc_array(descs), len(descs), _ptr(state_dev), _ptr(dt_dev),
                                            _stream(stream)))
+
+
+def hydro_server_create(pool_dev, pool_bytes: int, max_active: int, dry_run: bool = False) -> int:
+    cfg = hydro_server_config(_ptr(pool_dev), int(pool_bytes), int(max_active), int(bool(dry_run)))
+    s = _VP()
+    _check(load().hydro_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def hydro_server_destroy(s: int) -> None:
+    _check(load().hydro_server_destroy(s))
+
+
+def hydro_submit(s: int, desc: hydro_box_desc, ic: np.ndarray, nsteps: int) -> int:
+    ic = np.ascontiguousarray(ic, dtype=np.float64)
+    req = hydro_request(desc, ic.ctypes.data, int(nsteps))
+    t = ctypes.c_int64()
+    _check(load().hydro_submit(s, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def hydro_poll(s: int, ticket: int, out: np.ndarray | None = None):
+    """(status code, hydro_result); HYDRO_PENDING while the request runs.  A
+    failed request returns its (negative) error code and does not raise."""
+    info = hydro_result()
+    ptr = out.ctypes.data if out is not None else None
+    nbytes = out.nbytes if out is not None else 0
+    rc = load().hydro_poll(s, int(ticket), ptr, nbytes, ctypes.byref(info))
+    if rc < 0 and info.status == 0:
+        raise HydroError(rc, hydro_last_error())
+    return rc, info
+
+
+def hydro_server_get_stats(s: int) -> dict:
+    st = hydro_server_stats()
+    _check(load().hydro_server_get_stats(s, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in hydro_server_stats._fields_}
+
+
+class Server:
+    """A hydro server over a torch-allocated device pool (the memory budget)."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 256, device="cuda", dry_run: bool = False):
+        import torch
+        self.pool = None if dry_run else torch.empty((pool_bytes + 7) // 8, dtype=torch.float64, device=device)
+        self.s = hydro_server_create(self.pool, pool_bytes, max_active, dry_run)
+
+    def submit(self, problem, nsteps=None, precision=HYDRO_FP64) -> int:
+        n = problem.nsteps if nsteps is None else nsteps
+        return hydro_submit(self.s, desc_of(problem, precision), problem.U, n)
+
+    def wait(self, ticket, shape, timeout=600.0):
+        """Blocks until the request is done; returns (result array or None, hydro_result)."""
+        import time
+        nx, ny, nz = shape
+        out = np.zeros((5, nz, ny, nx))
+        t0 = time.monotonic()
+        while True:
+            rc, info = hydro_poll(self.s, ticket, out)
+            if rc != HYDRO_PENDING:
+                return (out if rc == HYDRO_OK else None), info
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+            time.sleep(0.0005)
+
+    def stats(self) -> dict:
+        return hydro_server_get_stats(self.s)
+
+    def close(self):
+        if self.s:
+            hydro_server_destroy(self.s)
+            self.s = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------ convenience
