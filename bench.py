@@ -223,6 +223,60 @@ def run_batched(hydro, inputs, torch, np, stream, nboxes=512, nsteps=30):
     return out
 
 
+# ------------------------------------------------------------ served stream
+def run_served(hydro, inputs, torch, np, nrequests, budget_gb=120.0, max_active=256):
+    """Continuous batching of a seeded request stream (Poisson arrivals at
+    200/s, box edges uniform in [32,128], 10-200 steps, Sod/Sedov/shear-layer
+    initial states, FP64 or mixed with equal odds) under a device memory
+    budget; requests are submitted at their arrival times through
+    hydro_submit and collected with hydro_poll."""
+    import time as _t
+    stream = inputs.served_stream(nrequests, seed=0)
+    work = sum(r.problem.zones * r.nsteps for r in stream)
+    torch.cuda.empty_cache()
+    srv = hydro.Server(int(budget_gb * 1e9), max_active=max_active)
+    outs = [np.zeros((5,) + r.problem.U.shape[1:]) for r in stream]
+    pending = {}
+    lat, queued = [], []
+    t0 = _t.perf_counter()
+    k = 0
+    while k < len(stream) or pending:
+        now = _t.perf_counter() - t0
+        while k < len(stream) and stream[k].arrival_s <= now:
+            r = stream[k]
+            prec = hydro.HYDRO_MIXED if r.mixed else hydro.HYDRO_FP64
+            pending[srv.submit(r.problem, nsteps=r.nsteps, precision=prec)] = k
+            k += 1
+        for t in list(pending):
+            rc, info = hydro.hydro_poll(srv.s, t, outs[pending[t]])
+            if rc == hydro.HYDRO_PENDING:
+                continue
+            if rc != hydro.HYDRO_OK:
+                raise RuntimeError(f"served request {pending[t]} failed: {rc}")
+            lat.append(info.latency_s)
+            queued.append(info.queued_s)
+            del pending[t]
+        _t.sleep(0.0002)
+    makespan = _t.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    del srv
+    torch.cuda.empty_cache()
+    span_arrivals = stream[-1].arrival_s
+    return {"workload": f"served_stream_{nrequests}", "requests": nrequests,
+            "offered_rate_req_per_s": 200.0,
+            "offered_zone_updates_per_s": work / span_arrivals if span_arrivals > 0 else None,
+            "value": work / makespan, "unit": UNIT, "makespan_s": makespan,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_queued_s": float(np.mean(queued)), "budget_gb": budget_gb, "max_active": max_active,
+            "peak_pool_gb": st["peak_bytes"] / 1e9, "ticks": st["ticks"],
+            "kernel_launches": st["kernel_launches"],
+            "mix": {"mixed": sum(r.mixed for r in stream),
+                    "sod": sum(r.problem.name == "sod" for r in stream),
+                    "sedov": sum(r.problem.name == "sedov" for r in stream),
+                    "kelvin_helmholtz": sum(r.problem.name == "kelvin_helmholtz" for r in stream)}}
+
+
 # ------------------------------------------------------------------ main arm
 def main() -> None:
     ap = argparse.ArgumentParser()
@@ -232,6 +286,8 @@ def main() -> None:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-box batched measurement")
+    ap.add_argument("--served-requests", type=int, default=48,
+                    help="length of the served request stream (0 skips it; the full stream is 2000)")
     ap.add_argument("--box", type=int, default=N_BOX, help="box edge (default 256; smaller only for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -344,6 +400,7 @@ def main() -> None:
     rel_l1 = {name: float(np.abs(mixed_final[v] - fp64_final[v]).sum() / np.abs(fp64_final[v]).sum())
               for name, v in (("rho", 0), ("E", 4))}
     batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
+    served = run_served(hydro, inputs, torch, np, args.served_requests) if args.served_requests > 0 else None
     mixed = {"value": world * N * args.steps / (ms_mixed * 1e-3), "unit": UNIT,
              "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
              "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
@@ -391,6 +448,7 @@ def main() -> None:
         "e2e": e2e,
         "mixed": mixed,
         "batched": batched,
+        "served": served,
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -208,3 +208,40 @@ def sedov_batch(nboxes=512, seed=0, gamma=1.4, cfl=0.5, nsteps=30, edges=BATCH_E
         shp = tuple(edges[min(int(r[3 * b + a] * len(edges)), len(edges) - 1)] for a in range(3))
         out.append(sedov(shp, seed=seed, box=b, gamma=gamma, cfl=cfl, nsteps=nsteps))
     return out
+
+
+@dataclass
+class ServedRequest:
+    arrival_s: float
+    problem: Problem
+    nsteps: int
+    mixed: bool
+
+
+def served_stream(nrequests=2000, seed=0, rate_per_s=200.0, edge_lo=32, edge_hi=128, steps_lo=10,
+                  steps_hi=200) -> list:
+    """A seeded stream of independent hydro requests: Poisson arrivals at
+    `rate_per_s`, box edges uniform in [edge_lo, edge_hi] per axis, step counts
+    uniform in [steps_lo, steps_hi], the initial condition drawn uniformly from
+    Sod (random axis and side), Sedov (random centre) and Kelvin-Helmholtz
+    (random perturbation seed), FP64 or mixed precision with equal odds."""
+    r = uniform01(seed, (1 << 23) + 1, np.arange(8 * nrequests, dtype=np.uint64)).reshape(nrequests, 8)
+    t = 0.0
+    out = []
+    span_e = edge_hi - edge_lo + 1
+    span_s = steps_hi - steps_lo + 1
+    for k in range(nrequests):
+        t += -np.log(1.0 - r[k, 0]) / rate_per_s
+        shape = tuple(edge_lo + min(int(r[k, 1 + a] * span_e), span_e - 1) for a in range(3))
+        nsteps = steps_lo + min(int(r[k, 4] * span_s), span_s - 1)
+        kind = min(int(r[k, 5] * 3), 2)
+        sub = r[k, 6]
+        if kind == 0:
+            axis = min(int(sub * 3), 2)
+            pr = sod(shape, axis=axis, flip=bool(int(sub * 6) % 2), nsteps=nsteps)
+        elif kind == 1:
+            pr = sedov(shape, seed=seed, box=k, nsteps=nsteps)
+        else:
+            pr = kelvin_helmholtz(shape, seed=seed + 1 + k, nsteps=nsteps)
+        out.append(ServedRequest(t, pr, nsteps, bool(r[k, 7] < 0.5)))
+    return out
