@@ -146,7 +146,7 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 /* Diagnostics: where the per-zone intermediates of box `box` live inside the
  * scratch buffer, for stage-by-stage checks.  *offset_bytes receives the byte
  * offset of the box's first field from the start of scratch_dev, *nfields the
- * number of fields (112) and *elem_bytes their element size (8 for
+ * number of fields (136) and *elem_bytes their element size (8 for
  * HYDRO_FP64, 4 for HYDRO_MIXED boxes).  Each field is a ghosted-box grid with
  * the state's pitch, plane and var_stride (in elements; fields are var_stride
  * elements apart), in this order: primitive q[5] = (rho,u,v,w,p); sound speed
@@ -154,7 +154,9 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
  * states qp[3][5] per axis d in the normal frame of d (rho, u_d, u_{d+1},
  * u_{d+2}, p, axis indices mod 3); normal fluxes f0[3][5]; once-corrected
  * fluxes f1[6][5] for the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes
- * f[3][5]; limited slopes dq[3][5] of the normal-frame variables of each axis.
+ * f[3][5]; limited slopes dq[3][5] of the normal-frame variables of each axis;
+ * conserved momenta (normal frame) and total energy of the left- and right-edge
+ * states, um[3][4] and up[3][4].
  * Fluxes are conserved-variable components; the flux through the low face of
  * zone (i,j,k) along d is stored at (i,j,k).  Values are defined only where
  * the step computes them. */
@@ -210,7 +212,7 @@ int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, in
  * allocation, or a latency-critical loop that cannot pay for cudaMalloc /
  * cudaFree (which may stall or synchronise the device).  hydro_compute_dt
  * needs a handle, and a handle needs a caller-allocated scratch buffer of
- * about 112 doubles per ghosted zone; this call needs neither.
+ * about 136 doubles per ghosted zone; this call needs neither.
  *
  * Writes dt_dev[b] = cfl * min over interior zones and axes of dx/(|u|+c)
  * for boxes d[0..nboxes-1] whose states sit in state_dev with the layout

@@ -26,7 +26,9 @@ constexpr double FLAT_OMEGA2 = 10.0;
 //   (rho, u_n, u_t1, u_t2, p with t1 = (d+1)%3, t2 = (d+2)%3),
 //   f0[d][5] normal fluxes, f1[pair][5] singly corrected fluxes for the ordered
 //   pairs (d,e) = xy,xz,yx,yz,zx,zy, f[d][5] final fluxes (conserved x,y,z order),
-//   dq[d][5] limited slopes of the normal-frame variables of axis d.
+//   dq[d][5] limited slopes of the normal-frame variables of axis d,
+//   um[d][4] / up[d][4] conserved momenta (normal frame) and total energy of
+//   the left-/right-edge states.
 // Flux of a d-face between zones Z-s_d and Z is stored at zone Z.
 enum Field : int {
   FLD_Q = 0,
@@ -38,7 +40,9 @@ enum Field : int {
   FLD_F1 = 52,
   FLD_F = 82,
   FLD_DQ = 97,
-  NFIELDS = 112
+  FLD_UM = 112,
+  FLD_UP = 124,
+  NFIELDS = 136
 };
 
 // Per-box geometry as the kernels see it (lives in the head of scratch).

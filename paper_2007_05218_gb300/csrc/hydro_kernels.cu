@@ -248,6 +248,29 @@ __device__ __forceinline__ R vl_slope(R am, R a0, R ap) {
   return copysign(from_bits(m), dc);
 }
 
+// FP64 form: the halving and doublings are exponent shifts of the bit
+// patterns, so the FP64 pipe only sees the three subtractions.  A shift is
+// exact only while the number and its result stay normal; differences near
+// the subnormal range (numerical tails ahead of a front decay that far) or
+// the overflow threshold take the multiplies instead.
+template <>
+__device__ __forceinline__ double vl_slope<double>(double am, double a0, double ap) {
+  const double dl = a0 - am, dr = ap - a0;
+  if (!same_sign(dl, dr)) return 0.0;
+  constexpr long long ONE_EXP = 1LL << 52, MAG = 0x7fffffffffffffffLL;
+  const double sum = ap - am;
+  const long long c = dbits(sum), l = dbits(dl) & MAG, r = dbits(dr) & MAG;
+  const long long ec = (c >> 52) & 0x7ff, el = l >> 52, er = r >> 52;
+  if (ec < 2 || el < 1 || er < 1 || el > 0x7fd || er > 0x7fd) {
+    const double dc = 0.5 * sum;
+    return copysign(fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr))), dc);
+  }
+  long long m = (c & MAG) - ONE_EXP;  // |ap - am| / 2
+  m = min(m, l + ONE_EXP);            // 2 |dl|
+  m = min(m, r + ONE_EXP);            // 2 |dr|
+  return from_bits(m | (c & ~MAG));   // sign of ap - am
+}
+
 // Limited slopes of the five normal-frame variables of axis D, once per zone
 // of [-2, n_D+1] along D and [-1, n] across it.
 template <typename R, int D>
@@ -302,9 +325,21 @@ __device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1,
   }
 }
 
+// Conserved momenta (normal frame) and total energy of a traced edge state,
+// stored once so that the Riemann and CTU stages need not rebuild them.
+template <typename R, int D>
+__device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs, long long Z, int base, const R* q,
+                                                R igm1) {
+  W[(base + 4 * D + 0) * vs + Z] = q[0] * q[1];
+  W[(base + 4 * D + 1) * vs + Z] = q[0] * q[2];
+  W[(base + 4 * D + 2) * vs + Z] = q[0] * q[3];
+  W[(base + 4 * D + 3) * vs + Z] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+}
+
 template <typename R, int D>
 __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
   const long long vs = b.vs, s = b.s[D];
+  const R igm1 = R(b.igm1);
   const R f = W[FLD_CHI * vs + Z];
   R a0[5], aL[5], aR[5];
 #pragma unroll
@@ -366,6 +401,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
+  store_conserved<R, D>(W, vs, Z, FLD_UP, out, igm1);
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
   if (is_neg(lm)) {
@@ -401,6 +437,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
+  store_conserved<R, D>(W, vs, Z, FLD_UM, out, igm1);
 }
 
 template <typename R>
@@ -421,7 +458,8 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 }
 
 // ----------------------------------------------------------------------- HLLC
-// Normal-frame states (rho, u_n, u_t1, u_t2, p) -> normal-frame flux.
+// Normal-frame states (rho, u_n, u_t1, u_t2, p) with their total energies
+// El, Er -> normal-frame flux.
 // Toro, Spruce & Speares 1994 with Roe-averaged bounds (Batten et al. 1997),
 // Davis bounds when the Roe sound speed is not real.  Only the star state on
 // the side of the contact that contains x/t = 0 is formed.  All square roots
@@ -430,7 +468,7 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // and three reciprocals; wave-speed min/max and sign tests run on the integer
 // pipe.
 template <typename R>
-__device__ __forceinline__ void hllc(const R* L, const R* Rs, R gamma, R igm1, R* F) {
+__device__ __forceinline__ void hllc(const R* L, R El, const R* Rs, R Er, R gamma, R* F) {
   const R gm1 = gamma - R(1);
   const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
   const R rr = Rs[0], ur = Rs[1], vr = Rs[2], wr = Rs[3], pr = Rs[4];
@@ -439,8 +477,6 @@ __device__ __forceinline__ void hllc(const R* L, const R* Rs, R gamma, R igm1, R
   const R irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
   const R gpl = gamma * pl, gpr = gamma * pr;
   const R cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
-  const R El = pl * igm1 + R(0.5) * rl * (ul * ul + vl * vl + wl * wl);
-  const R Er = pr * igm1 + R(0.5) * rr * (ur * ur + vr * vr + wr * wr);
   const R iw = nr_rcp(sl + sr);
   const R wgl = sl * iw, wgr = sr * iw;
   const R ut = wgl * ul + wgr * ur;
@@ -484,13 +520,20 @@ __device__ __forceinline__ void hllc(const R* L, const R* Rs, R gamma, R igm1, R
   }
 }
 
+// The two states of the D-face at zone Z: primitive q (5) and conserved
+// momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides.
 template <typename R, int D>
 __device__ __forceinline__ void load_face_states(const R* __restrict__ W, long long vs, long long Z, long long sD,
-                                                 R* qL, R* qR) {
+                                                 R* qL, R* uL, R* qR, R* uR) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     qL[m] = W[(FLD_QP + 5 * D + m) * vs + Z - sD];
     qR[m] = W[(FLD_QM + 5 * D + m) * vs + Z];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    uL[j] = W[(FLD_UP + 4 * D + j) * vs + Z - sD];
+    uR[j] = W[(FLD_UM + 4 * D + j) * vs + Z];
   }
 }
 
@@ -502,9 +545,9 @@ __device__ __forceinline__ void store_flux(R* __restrict__ dst, long long vs, lo
 
 template <typename R, int D>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
-  R qL[5], qR[5], Fn[5];
-  load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, qR);
-  hllc(qL, qR, R(b.gamma), R(b.igm1), Fn);
+  R qL[5], qR[5], uL[4], uR[4], Fn[5];
+  load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, uL, qR, uR);
+  hllc(qL, uL[3], qR, uR[3], R(b.gamma), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
@@ -528,18 +571,14 @@ __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __r
 }
 
 // ------------------------------------------------------------ CTU corrections
-// Face state q (normal frame of D) of the zone Z -> conserved, minus
-// fac_t * (flux difference across zone Z along stride s_t) for each term t,
-// -> primitive.  A result with rho <= 0 or p <= 0 keeps the uncorrected state.
+// Face state of zone Z (primitive q and conserved momenta + energy u, normal
+// frame of D) minus fac_t * (flux difference across zone Z along stride s_t)
+// for each term t, back to primitive.  A result with rho <= 0 or p <= 0 keeps
+// the uncorrected state.  Returns the total energy of the state that is kept.
 template <typename R, int D, int NT>
-__device__ __forceinline__ void correct(R* q, const R* const* Fb, const long long* st, const R* fac, long long vs,
-                                        long long Z, R gamma, R igm1) {
-  R U[5];
-  U[0] = q[0];
-  U[1] = q[0] * q[1];
-  U[2] = q[0] * q[2];
-  U[3] = q[0] * q[3];
-  U[4] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+__device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
+                                     long long vs, long long Z, R gamma, R igm1) {
+  R U[5] = {q[0], u[0], u[1], u[2], u[3]};
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const long long off = comp<D>(m) * vs + Z;
@@ -548,16 +587,23 @@ __device__ __forceinline__ void correct(R* q, const R* const* Fb, const long lon
   }
   if (is_pos(U[0])) {
     const R ir = nr_rcp(U[0]);
-    const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    const R p = (gamma - R(1)) * (U[4] - R(0.5) * U[0] * (u * u + v * v + w * w));
+    const R uu = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const R kin = R(0.5) * U[0] * (uu * uu + v * v + w * w);
+    const R p = (gamma - R(1)) * (U[4] - kin);
     if (is_pos(p)) {
       q[0] = U[0];
-      q[1] = u;
+      q[1] = uu;
       q[2] = v;
       q[3] = w;
-      q[4] = dgt(R(SMALL_PRES), p) ? R(SMALL_PRES) : p;
+      if (dgt(R(SMALL_PRES), p)) {  // floored pressure: the energy follows it
+        q[4] = R(SMALL_PRES);
+        return q[4] * igm1 + kin;
+      }
+      q[4] = p;
+      return U[4];
     }
   }
+  return u[3];
 }
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
@@ -566,14 +612,14 @@ template <typename R, int D, int E>
 __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, double dt) {
   const long long vs = b.vs, sD = b.s[D];
   const R gamma = R(b.gamma), igm1 = R(b.igm1);
-  R qL[5], qR[5], Fn[5];
-  load_face_states<R, D>(W, vs, Z, sD, qL, qR);
+  R qL[5], qR[5], uL[4], uR[4], Fn[5];
+  load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
   const R* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
   const long long st[1] = {b.s[E]};
   const R fac[1] = {R(dt * b.idx[E] * (1.0 / 3.0))};
-  correct<R, D, 1>(qL, Fb, st, fac, vs, Z - sD, gamma, igm1);
-  correct<R, D, 1>(qR, Fb, st, fac, vs, Z, gamma, igm1);
-  hllc(qL, qR, gamma, igm1, Fn);
+  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
+  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
+  hllc(qL, EL, qR, ER, gamma, Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
 }
 
@@ -609,14 +655,14 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
   const long long vs = b.vs, sD = b.s[D];
   const R gamma = R(b.gamma), igm1 = R(b.igm1);
-  R qL[5], qR[5], Fn[5];
-  load_face_states<R, D>(W, vs, Z, sD, qL, qR);
+  R qL[5], qR[5], uL[4], uR[4], Fn[5];
+  load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
   const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
   const R fac[2] = {R(0.5 * dt * b.idx[E]), R(0.5 * dt * b.idx[F])};
-  correct<R, D, 2>(qL, Fb, st, fac, vs, Z - sD, gamma, igm1);
-  correct<R, D, 2>(qR, Fb, st, fac, vs, Z, gamma, igm1);
-  hllc(qL, qR, gamma, igm1, Fn);
+  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
+  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
+  hllc(qL, EL, qR, ER, gamma, Fn);
   if (wall) {
     // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
     Fn[0] = R(0);
@@ -680,7 +726,7 @@ __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __re
   double nu[5];
   if (b.precision == HYDRO_FP64) update_zone(b, U, fields<double>(work, b), Z, dt, nu);
   else update_zone(b, U, fields<float>(work, b), Z, dt, nu);
-  const double kin = 0.5 * (nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3]) / nu[0];
+  const double kin = 0.5 * (nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3]) * nr_rcp(nu[0]);
   const double p = (b.gamma - 1.0) * (nu[4] - kin);
   if (!(nu[0] > 0.0) || !(p > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
 }

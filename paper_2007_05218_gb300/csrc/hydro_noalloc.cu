@@ -1,7 +1,7 @@
 // Allocation-free variant of the CFL time-step reduction.
 //
 // hydro_compute_dt works on a handle whose scratch buffer the caller has to
-// allocate (about 112 doubles per ghosted zone).  Some callers cannot allocate
+// allocate (about 136 doubles per ghosted zone).  Some callers cannot allocate
 // device memory at the point where they need a time step: a process that
 // hands all device memory to its own pool at start-up and permits no further
 // allocation, or a latency-critical loop that cannot pay for cudaMalloc /
