@@ -502,8 +502,6 @@ __device__ __forceinline__ void hllc(const R* L, R El, const R* Rs, R Er, R gamm
   const R mu = rK * uK;
   F[0] = mu;
   F[1] = mu * uK + pK;
-  F[2] = mu * vK;
-  F[3] = mu * wK;
   F[4] = (EK + pK) * uK;
   const bool supersonic = left ? is_nonneg(SL) : !is_pos(SR);
   if (!supersonic) {
@@ -514,10 +512,12 @@ __device__ __forceinline__ void hllc(const R* L, R El, const R* Rs, R Er, R gamm
     const R eK = EK * irK + (Ss - uK) * (Ss + pK * den * r);
     F[0] += SK * (fac - rK);
     F[1] += SK * (fac * Ss - mu);
-    F[2] += SK * (fac * vK - rK * vK);
-    F[3] += SK * (fac * wK - rK * wK);
     F[4] += SK * (fac * eK - EK);
   }
+  // the upwind side's star and outer states share its transverse velocity, so
+  // the transverse momentum fluxes are the mass flux times that velocity
+  F[2] = F[0] * vK;
+  F[3] = F[0] * wK;
 }
 
 // The two states of the D-face at zone Z: primitive q (5) and conserved
@@ -695,6 +695,20 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
 }
 
 // --------------------------------------------------------------------- update
+// FP32 -> FP64 on the integer pipe (the conversion instruction would occupy
+// the FP64 pipe): exact for normal floats; zero, subnormal floats (below
+// 1.2e-38) give zero.  Both neighbours of a face widen its flux identically,
+// so conservation is untouched.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned int f = __float_as_uint(x);
+  const unsigned int e = (f >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long mag = ((unsigned long long)(f & 0x7fffffffu) << 29) + (896ull << 52);
+  return __longlong_as_double((long long)(sign | mag));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // FP64 for every box; the fluxes are read in the box's compute type.
 template <typename R>
 __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict__ U, const R* __restrict__ W,
@@ -707,7 +721,7 @@ __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict_
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       const R* F = W + (FLD_F + 5 * d + v) * vs;
-      val = val - dtdx[d] * ((double)F[Z + b.s[d]] - (double)F[Z]);
+      val = val - dtdx[d] * (widen(F[Z + b.s[d]]) - widen(F[Z]));
     }
     nu[v] = val;
     U[v * vs + Z] = val;
