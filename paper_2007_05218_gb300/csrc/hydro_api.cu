@@ -355,6 +355,8 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
     }
     db.gamma = hb.d.gamma;
     db.igm1 = 1.0 / (hb.d.gamma - 1.0);
+    db.gamma_f = (float)db.gamma;
+    db.igm1_f = (float)db.igm1;
     db.cfl = hb.d.cfl;
     for (int f = 0; f < 6; f++) db.bc[f] = hb.d.bc[f];
     p.max_interior = std::max(p.max_interior, hb.interior);

@@ -60,7 +60,7 @@ struct DevBox {
   double igm1;            // 1/(gamma-1)
   double cfl;
   int bc[6];
-  int pad[2];
+  float gamma_f, igm1_f;  // FP32 copies for the mixed-precision kernels
 };
 
 // Per-box runtime record (lives in scratch, after the box table).
@@ -70,6 +70,8 @@ struct BoxRt {
   double time;              // simulated time advanced so far
   unsigned int status;      // device error flags (STATUS_*)
   unsigned int steps;       // updates applied
+  float dtdx_f[3];          // FP32 dt/dx per axis for the mixed-precision kernels
+  float pad;
 };
 
 constexpr unsigned STATUS_NONPHYSICAL = 1u;

@@ -50,6 +50,23 @@ __device__ __forceinline__ bool box_uses<double>(const DevBox& b) { return b.pre
 template <>
 __device__ __forceinline__ bool box_uses<float>(const DevBox& b) { return b.precision == HYDRO_MIXED; }
 
+// Per-box constants in the compute type: FP64 kernels read the doubles, FP32
+// kernels the float copies (a double->float conversion occupies the FP64 pipe).
+template <typename R>
+struct Consts;
+template <>
+struct Consts<double> {
+  static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
+  static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
+  static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
+};
+template <>
+struct Consts<float> {
+  static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
+  static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
+  static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
+};
+
 template <typename R>
 __device__ __forceinline__ R* fields(unsigned char* work, const DevBox& b) {
   return reinterpret_cast<R*>(work + b.work_off);
@@ -194,6 +211,7 @@ __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, i
     const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
     rt[b].smax = 0ull;
     rt[b].dt = dt;
+    for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
     if (dt_out) dt_out[b] = dt;
     if (advance) {
       rt[b].time += dt;
@@ -339,7 +357,7 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
 template <typename R, int D>
 __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
   const long long vs = b.vs, s = b.s[D];
-  const R igm1 = R(b.igm1);
+  const R igm1 = Consts<R>::igm1(b);
   const R f = W[FLD_CHI * vs + Z];
   R a0[5], aL[5], aR[5];
 #pragma unroll
@@ -449,11 +467,11 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[bi].dt;
+  const BoxRt& r = rt[bi];
   switch (z_) {
-    case 0: trace_zone<R, 0>(b, W, Z, R(dt * b.idx[0])); break;
-    case 1: trace_zone<R, 1>(b, W, Z, R(dt * b.idx[1])); break;
-    default: trace_zone<R, 2>(b, W, Z, R(dt * b.idx[2])); break;
+    case 0: trace_zone<R, 0>(b, W, Z, Consts<R>::dtdx(b, r, 0)); break;
+    case 1: trace_zone<R, 1>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
+    default: trace_zone<R, 2>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
   }
 }
 
@@ -547,7 +565,7 @@ template <typename R, int D>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, uL, qR, uR);
-  hllc(qL, uL[3], qR, uR[3], R(b.gamma), Fn);
+  hllc(qL, uL[3], qR, uR[3], Consts<R>::gamma(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
@@ -609,14 +627,14 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
 
 template <typename R, int D, int E>
-__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, double dt) {
+__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt) {
   const long long vs = b.vs, sD = b.s[D];
-  const R gamma = R(b.gamma), igm1 = R(b.igm1);
+  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
   const R* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
   const long long st[1] = {b.s[E]};
-  const R fac[1] = {R(dt * b.idx[E] * (1.0 / 3.0))};
+  const R fac[1] = {Consts<R>::dtdx(b, rt, E) * R(1.0 / 3.0)};
   const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
   const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
   hllc(qL, EL, qR, ER, gamma, Fn);
@@ -639,27 +657,28 @@ __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __rest
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[bi].dt;
+  const BoxRt& rtb = rt[bi];
   switch (p) {
-    case 0: ctu1_face<R, 0, 1>(b, W, Z, dt); break;
-    case 1: ctu1_face<R, 0, 2>(b, W, Z, dt); break;
-    case 2: ctu1_face<R, 1, 0>(b, W, Z, dt); break;
-    case 3: ctu1_face<R, 1, 2>(b, W, Z, dt); break;
-    case 4: ctu1_face<R, 2, 0>(b, W, Z, dt); break;
-    default: ctu1_face<R, 2, 1>(b, W, Z, dt); break;
+    case 0: ctu1_face<R, 0, 1>(b, W, Z, rtb); break;
+    case 1: ctu1_face<R, 0, 2>(b, W, Z, rtb); break;
+    case 2: ctu1_face<R, 1, 0>(b, W, Z, rtb); break;
+    case 3: ctu1_face<R, 1, 2>(b, W, Z, rtb); break;
+    case 4: ctu1_face<R, 2, 0>(b, W, Z, rtb); break;
+    default: ctu1_face<R, 2, 1>(b, W, Z, rtb); break;
   }
 }
 
 template <typename R, int D>
-__device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, long long Z, double dt, bool wall) {
+__device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
+                                          bool wall) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
   const long long vs = b.vs, sD = b.s[D];
-  const R gamma = R(b.gamma), igm1 = R(b.igm1);
+  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
   const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
-  const R fac[2] = {R(0.5 * dt * b.idx[E]), R(0.5 * dt * b.idx[F])};
+  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
   const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
   const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
   hllc(qL, EL, qR, ER, gamma, Fn);
@@ -684,13 +703,13 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  const double dt = rt[bi].dt;
+  const BoxRt& r = rt[bi];
   const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT) ||
                     (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT);
   switch (d) {
-    case 0: ctu2_face<R, 0>(b, W, Z, dt, wall); break;
-    case 1: ctu2_face<R, 1>(b, W, Z, dt, wall); break;
-    default: ctu2_face<R, 2>(b, W, Z, dt, wall); break;
+    case 0: ctu2_face<R, 0>(b, W, Z, r, wall); break;
+    case 1: ctu2_face<R, 1>(b, W, Z, r, wall); break;
+    default: ctu2_face<R, 2>(b, W, Z, r, wall); break;
   }
 }
 

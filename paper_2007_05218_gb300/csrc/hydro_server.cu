@@ -187,6 +187,8 @@ hydro::DevBox dev_box(const Request* r) {
   }
   db.gamma = hb.d.gamma;
   db.igm1 = 1.0 / (hb.d.gamma - 1.0);
+  db.gamma_f = (float)db.gamma;
+  db.igm1_f = (float)db.igm1;
   db.cfl = hb.d.cfl;
   for (int f = 0; f < 6; f++) db.bc[f] = hb.d.bc[f];
   return db;
