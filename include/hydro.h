@@ -163,6 +163,25 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset_bytes, int32_t* nfields,
                        int32_t* elem_bytes);
 
+/* ---- boxes of one domain ----
+ * A domain (one refinement level, the paper's MultiFab of boxes, §2) is a set
+ * of boxes whose ghost zones on internal faces come from the neighbouring
+ * box's interior instead of a boundary condition.  neighbors[6*b + f] is the
+ * index of the box across face f (xlo, xhi, ylo, yhi, zlo, zhi) of box b, or
+ * -1 to use the box's boundary condition on that face (periodic wrap of the
+ * whole domain is expressed by linking the boxes at its two ends).  A
+ * neighbour must have the same extents across the face, the same zone widths
+ * and gamma; the descriptor's bc of a linked face is ignored.  The ghost fill
+ * runs in x, then y, then z over all boxes, so edges and corners come from
+ * the right boxes.  Synchronous; returns HYDRO_ERR_INVALID on a bad table.
+ *
+ * hydro_set_shared_dt(h, 1) makes every box advance with one dt per step, the
+ * minimum over the boxes of their CFL steps (dt_dev == NULL in hydro_step),
+ * as a level of one domain must.  A domain split into boxes then advances
+ * exactly (bitwise) like the same domain in one box. */
+int hydro_set_neighbors(hydro_handle* h, const int32_t* neighbors);
+int hydro_set_shared_dt(hydro_handle* h, int enable);
+
 /* Launch configuration.  Every stage kernel covers all boxes of the handle in
  * one launch: the boxes' blocks are packed back to back through a work table
  * in the scratch head (block -> box and axis), so uneven boxes waste no

@@ -24,6 +24,7 @@ struct hydro_handle {
   std::vector<cudaEvent_t> events;   // event pool (pairs), reused across sessions
   std::vector<int> rec_stage;        // stage of each recorded pair
   std::vector<int> rec_kernels;      // kernels launched inside each recorded pair
+  std::vector<DevBox> dbox_host;     // host copy of the device box table
   // one step captured as a CUDA graph and replayed by hydro_step
   bool use_graphs = true;
   cudaStream_t capture_stream = nullptr;
@@ -364,6 +365,7 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
     else p.has_fp64 = true;
     p.max_ghosted = std::max(p.max_ghosted, hb.vs);
   }
+  h->dbox_host = table;
   e = cudaMemcpy(p.dboxes, table.data(), sizeof(DevBox) * nboxes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p.rt, 0, sizeof(BoxRt) * nboxes);
   for (int t = 0; t < hydro::NTABLES && e == cudaSuccess; t++)
@@ -498,6 +500,49 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
   if (e == cudaSuccess) e = cudaMemcpyAsync(state_host, stage, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return launched(e, "hydro_download");
+}
+
+int hydro_set_neighbors(hydro_handle* h, const int32_t* neighbors) {
+  if (!h || !neighbors) return fail(HYDRO_ERR_INVALID, "null argument");
+  int rc = check_device(h);
+  if (rc) return rc;
+  const int n = h->plan.nboxes;
+  std::vector<DevBox> t = h->dbox_host;
+  for (int b = 0; b < n; b++)
+    for (int f = 0; f < 6; f++) {
+      const int o = neighbors[6 * b + f];
+      char buf[160];
+      if (o < -1 || o >= n) {
+        snprintf(buf, sizeof buf, "box %d face %d: neighbour %d out of range", b, f, o);
+        return fail(HYDRO_ERR_INVALID, buf);
+      }
+      t[b].nbr1[f] = o + 1;
+      if (o < 0) continue;
+      const int d = f / 2, e = (d + 1) % 3, g = (d + 2) % 3;
+      const hydro_box_desc &A = h->boxes[b].d, &B = h->boxes[o].d;
+      const int na[3] = {A.nx, A.ny, A.nz}, nb[3] = {B.nx, B.ny, B.nz};
+      const double da[3] = {A.dx, A.dy, A.dz}, db[3] = {B.dx, B.dy, B.dz};
+      if (na[e] != nb[e] || na[g] != nb[g] || nb[d] < HYDRO_NG) {
+        snprintf(buf, sizeof buf, "box %d face %d: neighbour %d must match its extents across the face", b, f, o);
+        return fail(HYDRO_ERR_INVALID, buf);
+      }
+      if (da[0] != db[0] || da[1] != db[1] || da[2] != db[2] || A.gamma != B.gamma) {
+        snprintf(buf, sizeof buf, "box %d face %d: neighbour %d has other zone widths or gamma", b, f, o);
+        return fail(HYDRO_ERR_INVALID, buf);
+      }
+    }
+  cudaError_t e = cudaMemcpy(h->plan.dboxes, t.data(), sizeof(DevBox) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_set_neighbors");
+  h->dbox_host = t;
+  drop_graph(h);
+  return HYDRO_OK;
+}
+
+int hydro_set_shared_dt(hydro_handle* h, int enable) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  h->plan.shared_dt = enable != 0;
+  drop_graph(h);
+  return HYDRO_OK;
 }
 
 int hydro_use_graphs(hydro_handle* h, int enable) {

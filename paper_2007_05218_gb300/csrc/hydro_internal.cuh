@@ -61,6 +61,8 @@ struct DevBox {
   double cfl;
   int bc[6];
   float gamma_f, igm1_f;  // FP32 copies for the mixed-precision kernels
+  int nbr1[6];            // per face: 1 + index of the box whose interior fills its ghosts, 0: use bc
+  int pad2[2];
 };
 
 // Per-box runtime record (lives in scratch, after the box table).
@@ -130,6 +132,7 @@ struct Plan {
   int max_n[3];        // max interior extent per axis over boxes
   long long max_ghosted, max_interior;
   WorkTable tab[NTABLES][2];  // [table][0: FP64 boxes (or all boxes), 1: mixed boxes]
+  bool shared_dt = false;     // one dt for all boxes: the minimum of their CFL steps
 };
 
 // Threads per block each table starts with (before any autotuning).

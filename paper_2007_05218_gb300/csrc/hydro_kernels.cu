@@ -132,6 +132,22 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
   const int l = c[D], n = b.n[D];
   const int side = l < NG ? 0 : 1;
   const int m = side == 0 ? NG - l : l - NG + 1;  // depth 1..NG
+  const int nb1 = b.nbr1[2 * D + side];
+  double* U = state + b.state_off;
+  if (nb1 > 0) {
+    // a neighbouring box of the same domain: copy its interior layer at depth m
+    // (its extents across D equal this box's, its strides may differ)
+    const DevBox& o = boxes[nb1 - 1];
+    const int src = side == 0 ? o.n[D] - m : m - 1;
+    c[D] = side == 0 ? -m : n - 1 + m;
+    const long long zg = zone(b, c[0], c[1], c[2]);
+    c[D] = src;
+    const long long zs = zone(o, c[0], c[1], c[2]);
+    const double* S = state + o.state_off;
+#pragma unroll
+    for (int v = 0; v < 5; v++) U[v * b.vs + zg] = S[v * o.vs + zs];
+    return;
+  }
   const int bc = b.bc[2 * D + side];
   int src;
   if (bc == HYDRO_BC_PERIODIC) src = side == 0 ? n - m : m - 1;
@@ -141,7 +157,6 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
   const long long zg = zone(b, c[0], c[1], c[2]);
   c[D] = src;
   const long long zs = zone(b, c[0], c[1], c[2]);
-  double* U = state + b.state_off;
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     double val = U[v * b.vs + zs];
@@ -209,6 +224,36 @@ __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, i
     if (boxes[b].n[0] == 0) continue;  // a free slot of a server plan
     const double smax = __longlong_as_double((long long)rt[b].smax);
     const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
+    rt[b].smax = 0ull;
+    rt[b].dt = dt;
+    for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
+    if (dt_out) dt_out[b] = dt;
+    if (advance) {
+      rt[b].time += dt;
+      rt[b].steps += 1u;
+    }
+  }
+}
+
+// One dt for all boxes of a domain (an AMR level advanced together): the
+// minimum over boxes of cfl_b / smax_b.  One block.
+__global__ void __launch_bounds__(256) k_dt_shared(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt,
+                                                   int nboxes, double* __restrict__ dt_out, int advance) {
+  __shared__ double red[256];
+  double m = HUGE_VAL;
+  for (int b = threadIdx.x; b < nboxes; b += blockDim.x) {
+    if (boxes[b].n[0] == 0) continue;
+    m = fmin(m, boxes[b].cfl / __longlong_as_double((long long)rt[b].smax));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double dt = red[0];
+  for (int b = threadIdx.x; b < nboxes; b += blockDim.x) {
+    if (boxes[b].n[0] == 0) continue;
     rt[b].smax = 0ull;
     rt[b].dt = dt;
     for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
@@ -704,8 +749,8 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   const BoxRt& r = rt[bi];
-  const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT) ||
-                    (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT);
+  const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT && b.nbr1[2 * d] == 0) ||
+                    (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * d + 1] == 0);
   switch (d) {
     case 0: ctu2_face<R, 0>(b, W, Z, r, wall); break;
     case 1: ctu2_face<R, 1>(b, W, Z, r, wall); break;
@@ -891,7 +936,10 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
       n += launch(k_prim, T[TB_PRIM][0], stream, p.dboxes, (const double*)p.state, p.work, p.rt);
       break;
     case ST_DT:
-      k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
+      if (p.shared_dt && !dt_in)
+        k_dt_shared<<<1, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_out, advance);
+      else
+        k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
       n = 1;
       break;
     case ST_FLATTEN:

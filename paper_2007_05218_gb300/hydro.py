@@ -34,7 +34,7 @@ EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_fr
             "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
             "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
             "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
-            "hydro_server_get_stats", "hydro_last_error")
+            "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -120,6 +120,8 @@ def load(path: str | None = None):
         L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
         L.hydro_autotune.argtypes = [_VP, i, ctypes.POINTER(hydro_tuning), i, ctypes.POINTER(i), _VP]
         L.hydro_use_graphs.argtypes = [_VP, i]
+        L.hydro_set_neighbors.argtypes = [_VP, _VP]
+        L.hydro_set_shared_dt.argtypes = [_VP, i]
         L.hydro_server_create.argtypes = [ctypes.POINTER(hydro_server_config), ctypes.POINTER(_VP)]
         L.hydro_server_destroy.argtypes = [_VP]
         L.hydro_submit.argtypes = [_VP, ctypes.POINTER(hydro_request), ctypes.POINTER(ctypes.c_int64)]
@@ -272,6 +274,16 @@ def hydro_autotune(h: int, reps: int = 3, stream=None) -> list:
     n = ctypes.c_int()
     _check(load().hydro_autotune(h, int(reps), buf, 64, ctypes.byref(n), _stream(stream)))
     return [(buf[k].name.decode(), buf[k].precision, buf[k].threads, buf[k].order, buf[k].ms) for k in range(n.value)]
+
+
+def hydro_set_neighbors(h: int, neighbors) -> None:
+    """neighbors: int array [nboxes][6] of neighbour box indices (-1: boundary condition)."""
+    nb = np.ascontiguousarray(neighbors, dtype=np.int32)
+    _check(load().hydro_set_neighbors(h, nb.ctypes.data))
+
+
+def hydro_set_shared_dt(h: int, enable: bool) -> None:
+    _check(load().hydro_set_shared_dt(h, int(bool(enable))))
 
 
 def hydro_use_graphs(h: int, enable: bool) -> None:
