@@ -53,11 +53,16 @@ _D = ctypes.POINTER(ctypes.c_double)
 
 
 def lib():
+    """The oracle library; HYDRO_ORACLE_LIB may name another build of it (the
+    mutation tests load deliberately broken copies that way)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(LIB_PATH)
+            path = os.environ.get("HYDRO_ORACLE_LIB")
+            if not path:
+                build()
+                path = LIB_PATH
+            L = ctypes.CDLL(path)
             P = ctypes.POINTER(ObBox)
             L.oracle_fill_ghosts.argtypes = [P, _D]
             L.oracle_compute_dt.argtypes = [P, _D, _D]

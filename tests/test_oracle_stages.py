@@ -264,3 +264,58 @@ def test_dt_closed_form_on_uniform_state():
     c = np.sqrt(GAMMA * 0.7 / 1.3)
     expect = 0.5 * min(0.1 / (0.3 + c), 0.05 / (0.9 + c), 0.2 / (0.1 + c))
     assert dt == pytest.approx(expect, rel=1e-14)
+
+
+def _parabola_mean(aL, aR, a0, lo, hi):
+    """Mean of the zone parabola over [lo, hi] of the zone's unit interval (quadrature)."""
+    a6 = 6 * (a0 - 0.5 * (aL + aR))
+    xg, wg = np.polynomial.legendre.leggauss(4)
+    xi = lo + 0.5 * (hi - lo) * (xg + 1)
+    return 0.5 * np.sum(wg * (aL + xi * (aR - aL + a6 * (1 - xi))))
+
+
+@pytest.mark.parametrize("u0", [2.2, 0.4, -0.4, -2.2])
+def test_tracing_projects_each_characteristic_on_its_own_upwind_average(u0):
+    """Characteristic tracing: with the zone-centred left eigenvectors
+    l- = (0, -rho/2c, 1/2c^2), l0 = (1, 0, -1/c^2), l+ = (0, rho/2c, 1/2c^2) in
+    (rho, u_n, p), each wave that reaches an edge carries its own upwind average
+    of the parabolas to it, l.q_edge = l.I(sigma_wave), and a wave that does
+    not reach leaves l.q_edge = l.q_ref.  Sub- and supersonic, both directions."""
+    n = 24
+    x = np.linspace(0, 1, n)
+    q = np.empty((5, n))
+    q[0] = 1.0 + 0.2 * np.sin(5 * x)
+    q[1] = u0 + 0.1 * np.cos(3 * x)
+    q[2] = 0.1 * np.sin(2 * x)
+    q[3] = -0.2 * x * x
+    q[4] = 1.0 + 0.1 * np.cos(4 * x)
+    c = np.sqrt(GAMMA * q[4] / q[0])
+    dtdx = 0.15
+    qm, qp = oracle.trace_line(q, c, np.zeros(n), dtdx)
+    par = [oracle.ppm_line(q[m]) for m in range(5)]
+    for i in range(3, n - 3):
+        rho, u, cs = q[0, i], q[1, i], c[i]
+        lvec = {-1: np.array([0.0, -rho / (2 * cs), 1 / (2 * cs * cs)]),
+                0: np.array([1.0, 0.0, -1 / (cs * cs)]),
+                1: np.array([0.0, rho / (2 * cs), 1 / (2 * cs * cs)])}
+        lam = {-1: u - cs, 0: u, 1: u + cs}
+        for side, qe in ((0, qp), (1, qm)):
+            def avg(m, sig):
+                aL, aR = par[m][0][i], par[m][1][i]
+                return (_parabola_mean(aL, aR, q[m, i], 1 - sig, 1) if side == 0
+                        else _parabola_mean(aL, aR, q[m, i], 0, sig))
+            reaches = (lambda l: l > 0) if side == 0 else (lambda l: l < 0)
+            fast = 1 if side == 0 else -1
+            ref = ([avg(m, abs(lam[fast]) * dtdx) for m in range(5)] if reaches(lam[fast])
+                   else list(q[:, i]))
+            edge = np.array([qe[0, i], qe[1, i], qe[4, i]])
+            for nu in (-1, 0, 1):
+                if reaches(lam[nu]):
+                    sig = abs(lam[nu]) * dtdx
+                    target = np.array([avg(0, sig), avg(1, sig), avg(4, sig)])
+                else:
+                    target = np.array([ref[0], ref[1], ref[4]])
+                assert lvec[nu] @ edge == pytest.approx(lvec[nu] @ target, rel=1e-11, abs=1e-12), (i, side, nu)
+            for m in (2, 3):  # transverse velocities ride the entropy wave
+                expect = avg(m, abs(u) * dtdx) if reaches(lam[0]) else ref[m]
+                assert qe[m, i] == pytest.approx(expect, rel=1e-11, abs=1e-13)
