@@ -73,6 +73,8 @@ int oracle_count_step(int nx, int ny, int nz, const double* dx, double gamma, do
   b.gamma = cd(gamma);
   b.cfl = cd(cfl);
   for (int f = 0; f < 6; f++) b.bc[f] = bc[f];
+  b.limiter = 0;
+  b.riemann = 0;
   if (!box_ok(&b)) return -1;
   Grid G(&b);
   cd* U = (cd*)calloc((size_t)5 * G.size, sizeof(cd));

@@ -41,6 +41,25 @@
  *   R11 the final flux through a reflecting face carries no mass, energy or
  *       tangential momentum (the wall is impermeable; only the normal
  *       momentum flux, the wall pressure, is kept).
+ *   R13 limiter variant (box field limiter = 1): Colella & Sekora 2008 (CS08).
+ *       Interface values are the 4th-order interpolant of the four nearest
+ *       zone values; one that does not lie between its two zone values is
+ *       rebuilt from a limited second difference (CS08 §2.1).  The zone
+ *       parabola is then limited by CS08's extremum test (zone or its
+ *       neighbours at an extremum: curvature limited by the neighbouring
+ *       second differences, edges scaled toward the zone value), else by the
+ *       CW84 overshoot rule; C = 1.25; flattening blends afterwards as in R3.
+ *       No van Leer slopes are formed.
+ *   R14 Riemann variant (box field riemann = 1): two-shock approximation
+ *       (Colella & Glaz 1985): both nonlinear waves follow their shock
+ *       Hugoniot, p* is the root of the two-shock velocity balance found by
+ *       Newton's method from the acoustic guess (floor small_pres; stop when
+ *       the step is at most 1e-12 p*, at most 40 steps); u* is the mean of
+ *       the two sides' star velocities; star densities come from the
+ *       Hugoniot; the state at x/t = 0 is sampled on the side of the contact
+ *       that holds it (u* = 0 takes the left side), across a shock by its
+ *       speed, across a rarefaction by linear interpolation in x/t between
+ *       the head and tail states; the flux is the Euler flux of that state.
  *
  * Layout: every field is a [k][j][i] array over the ghosted box
  * (nx+2g)(ny+2g)(nz+2g), i fastest, no padding.  Conserved state
@@ -64,6 +83,8 @@ typedef struct {
   double gamma;     /* ratio of specific heats */
   double cfl;       /* Courant number */
   int bc[6];        /* xlo,xhi,ylo,yhi,zlo,zhi: 0 periodic, 1 outflow, 2 reflect */
+  int limiter;      /* 0 CW84 (R3), 1 Colella-Sekora (R13) */
+  int riemann;      /* 0 HLLC (R5), 1 two-shock (R14) */
 } ob_box;
 }
 
@@ -109,6 +130,7 @@ static int box_ok(const ob_box* b) {
     if ((lo == OB_PERIODIC) != (hi == OB_PERIODIC)) return 0;
     if (!(b->dx[a] > 0.0)) return 0;
   }
+  if (b->limiter < 0 || b->limiter > 1 || b->riemann < 0 || b->riemann > 1) return 0;
   return b->gamma > 1.0 && b->cfl > 0.0;
 }
 
@@ -260,6 +282,62 @@ static void limit_parabola(double a0, double f, double* aL, double* aR) {
   *aR = f * a0 + (1.0 - f) * R;
 }
 
+/* ------------------------------------------- a4 variant: CS08 limiter (R13) */
+static const double CS_C = 1.25;
+
+/* CS08's limited second difference: when d2 and every neighbouring second
+ * difference share a sign, the smallest of |d2| and C |others|, with the sign
+ * of d2; otherwise zero. */
+static double cs_limited_d2(double d2, const double* others, int n) {
+  double m = fabs(d2);
+  for (int k = 0; k < n; k++) {
+    if (!(d2 * others[k] > 0.0)) return 0.0;
+    m = fmin(m, CS_C * fabs(others[k]));
+  }
+  return copysign(m, d2);
+}
+
+/* Value at the interface between zones Z-s and Z (CS08 §2.1): the 4th-order
+ * interpolant, rebuilt from a limited second difference when it is not
+ * between the two zone values. */
+static double cs_interface(const double* a, long Z, long s) {
+  double am = a[Z - 2 * s], a0 = a[Z - s], a1 = a[Z], a2 = a[Z + s];
+  double v = 7.0 / 12.0 * (a0 + a1) - 1.0 / 12.0 * (am + a2);
+  if ((v - a0) * (a1 - v) < 0.0) {
+    double d2 = 3.0 * (a0 - 2.0 * v + a1);
+    double nb[2] = {am - 2.0 * a0 + a1, a0 - 2.0 * a1 + a2};
+    v = 0.5 * (a0 + a1) - cs_limited_d2(d2, nb, 2) / 6.0;
+  }
+  return v;
+}
+
+/* Parabola of zone Z of line a (stride s) between interface values (L, R):
+ * CS08's limiter (§2.2), then the flattening blend of R3. */
+static void cs_limit_parabola(const double* a, long Z, long s, double f, double* aL, double* aR) {
+  double a0 = a[Z], L = *aL, R = *aR;
+  double am = a[Z - s], ap = a[Z + s];
+  if ((R - a0) * (a0 - L) <= 0.0 || (ap - a0) * (a0 - am) <= 0.0) {
+    /* an extremum in the zone or at a neighbour: keep the parabola's shape,
+     * with its curvature limited by the second differences around it */
+    double d2 = 6.0 * (L + R - 2.0 * a0);
+    double nb[3] = {a[Z - 2 * s] - 2.0 * am + a0, am - 2.0 * a0 + ap, a0 - 2.0 * ap + a[Z + 2 * s]};
+    double lim = cs_limited_d2(d2, nb, 3);
+    if (d2 != 0.0) {
+      L = a0 + (L - a0) * (lim / d2);
+      R = a0 + (R - a0) * (lim / d2);
+    } else {
+      L = a0;
+      R = a0;
+    }
+  } else if (fabs(R - a0) >= 2.0 * fabs(L - a0)) {
+    R = a0 - 2.0 * (L - a0);
+  } else if (fabs(L - a0) >= 2.0 * fabs(R - a0)) {
+    L = a0 - 2.0 * (R - a0);
+  }
+  *aL = f * a0 + (1.0 - f) * L;
+  *aR = f * a0 + (1.0 - f) * R;
+}
+
 /* -------------------------------------------- a5: characteristic tracing (R4) */
 /* Average of the parabola over the part of the zone swept by a wave of
  * Courant number sig toward the right edge (Iplus) or the left edge (Iminus). */
@@ -278,13 +356,14 @@ static double i_minus(double aL, double aR, double a0, double sig) {
  * of the low face) and the right-edge state qp[5] (the left state of the high
  * face), both in the normal frame. */
 static void trace_zone(const double* const qn[5], const double* const face[5], const double* c, double f,
-                       long Z, long s, double dtdx, double* qm, double* qp) {
+                       long Z, long s, double dtdx, int limiter, double* qm, double* qp) {
   double aL[5], aR[5], a0[5];
   for (int m = 0; m < 5; m++) {
     a0[m] = qn[m][Z];
     aL[m] = face[m][Z];
     aR[m] = face[m][Z + s];
-    limit_parabola(a0[m], f, &aL[m], &aR[m]);
+    if (limiter == 1) cs_limit_parabola(qn[m], Z, s, f, &aL[m], &aR[m]);
+    else limit_parabola(a0[m], f, &aL[m], &aR[m]);
   }
   double rho = a0[0], u = a0[1], cs = c[Z];
   double lam[3] = {u - cs, u, u + cs};
@@ -396,14 +475,102 @@ static void hllc_normal(const double* L, const double* R, double gamma, double* 
   for (int m = 0; m < 5; m++) F[m] = FR[m] + SR * (Us[m] - Ur[m]);
 }
 
-/* HLLC across a face normal to d, states and flux in x,y,z components. */
-static void hllc_xyz(int d, const double* qL, const double* qR, double gamma, double* F) {
+/* ------------------------------------ a9 variant: two-shock solver (R14) */
+static const double TS_TOL = 1e-12;
+static const int TS_MAXIT = 40;
+
+/* Lagrangian speed (mass flux) of a shock from state (rho, p) to pressure ps:
+ * W^2 = rho ((gamma+1)/2 ps + (gamma-1)/2 p) (Rankine-Hugoniot). */
+static double shock_w(double rho, double p, double ps, double gamma) {
+  return sqrt(rho * (0.5 * (gamma + 1.0) * ps + 0.5 * (gamma - 1.0) * p));
+}
+
+/* Star pressure and velocity of the two-shock approximation; returns the
+ * number of Newton steps taken.  The velocity change across the wave of side
+ * K is (p - p_K) / W_K(p); p* balances u_L - that of L with u_R + that of R. */
+static int two_shock_star(const double* L, const double* R, double gamma, double* ps, double* us) {
+  double rl = L[0], ul = L[1], pl = L[4], rr = R[0], ur = R[1], pr = R[4];
+  double Cl = sqrt(gamma * pl * rl), Cr = sqrt(gamma * pr * rr);
+  double p = (Cr * pl + Cl * pr + Cl * Cr * (ul - ur)) / (Cl + Cr);
+  if (p < SMALL_PRES) p = SMALL_PRES;
+  int it = 0;
+  while (it < TS_MAXIT) {
+    double Wl = shock_w(rl, pl, p, gamma), Wr = shock_w(rr, pr, p, gamma);
+    double f = (p - pl) / Wl + (p - pr) / Wr + (ur - ul);
+    /* d/dp of (p - p_K)/W_K(p) = (1 - (p - p_K) dW_K/dp / W_K) / W_K, dW_K/dp = rho_K (gamma+1) / (4 W_K) */
+    double dl = (1.0 - (p - pl) * rl * (gamma + 1.0) / (4.0 * Wl * Wl)) / Wl;
+    double dr = (1.0 - (p - pr) * rr * (gamma + 1.0) / (4.0 * Wr * Wr)) / Wr;
+    double pn = p - f / (dl + dr);
+    if (pn < SMALL_PRES) pn = SMALL_PRES;
+    it++;
+    double step = fabs(pn - p);
+    p = pn;
+    if (step <= TS_TOL * p) break;
+  }
+  double Wl = shock_w(rl, pl, p, gamma), Wr = shock_w(rr, pr, p, gamma);
+  *ps = p;
+  *us = 0.5 * ((ul - (p - pl) / Wl) + (ur + (p - pr) / Wr));
+  return it;
+}
+
+/* State at x/t = 0 of the two-shock solution (normal frame). */
+static void two_shock_state(const double* L, const double* R, double gamma, double* q) {
+  double ps, us;
+  two_shock_star(L, R, gamma, &ps, &us);
+  int left = us >= 0.0;
+  const double* K = left ? L : R;
+  double sgn = left ? 1.0 : -1.0;   /* the side's wave moves with u - sgn c */
+  double rk = K[0], uk = K[1], pk = K[4];
+  double Wk = shock_w(rk, pk, ps, gamma);
+  double rs = 1.0 / (1.0 / rk - (ps - pk) / (Wk * Wk));  /* Hugoniot: [1/rho] = -[p]/W^2 */
+  double star[5] = {rs, us, K[2], K[3], ps};
+  double outer[5] = {rk, uk, K[2], K[3], pk};
+  /* speeds of the side's wave as seen from the interface, positive when
+   * the wave is on the side's own half (moving away from x/t = 0) */
+  double head, tail;
+  if (ps > pk) {
+    head = tail = Wk / rk - sgn * uk;   /* shock: |S - u_K| = W_K / rho_K */
+  } else {
+    head = sqrt(gamma * pk / rk) - sgn * uk;
+    tail = sqrt(gamma * ps / rs) - sgn * us;
+  }
+  if (head <= 0.0) {
+    for (int m = 0; m < 5; m++) q[m] = outer[m];   /* the wave has left x/t = 0 behind */
+  } else if (tail >= 0.0) {
+    for (int m = 0; m < 5; m++) q[m] = star[m];
+  } else {
+    /* x/t = 0 inside the fan: linear in x/t between head and tail */
+    double a = head / (head - tail);
+    for (int m = 0; m < 5; m++) q[m] = (1.0 - a) * outer[m] + a * star[m];
+  }
+}
+
+static void euler_flux(const double* q, double gamma, double* F) {
+  double r = q[0], u = q[1], v = q[2], w = q[3], p = q[4];
+  double E = p / (gamma - 1.0) + 0.5 * r * (u * u + v * v + w * w);
+  F[0] = r * u;
+  F[1] = r * u * u + p;
+  F[2] = r * u * v;
+  F[3] = r * u * w;
+  F[4] = (E + p) * u;
+}
+
+static void two_shock_normal(const double* L, const double* R, double gamma, double* F) {
+  double q[5];
+  two_shock_state(L, R, gamma, q);
+  euler_flux(q, gamma, F);
+}
+
+/* The box's Riemann solver across a face normal to d, states and flux in
+ * x,y,z components. */
+static void riemann_xyz(int solver, int d, const double* qL, const double* qR, double gamma, double* F) {
   double L[5], R[5], Fn[5];
   for (int m = 0; m < 5; m++) {
     L[m] = qL[comp(d, m)];
     R[m] = qR[comp(d, m)];
   }
-  hllc_normal(L, R, gamma, Fn);
+  if (solver == 1) two_shock_normal(L, R, gamma, Fn);
+  else hllc_normal(L, R, gamma, Fn);
   for (int m = 0; m < 5; m++) F[comp(d, m)] = Fn[m];
 }
 
@@ -463,7 +630,8 @@ static void limited_slopes_dir(const Grid& G, int d, const double* W, double* sl
       }
 }
 
-/* a4: interface values on the faces [-1, n_d+1] of axis d (one per face) */
+/* a4: interface values on the faces [-1, n_d+1] of axis d (one per face);
+ * slope is NULL under the CS08 limiter (R13) */
 static void interface_values_dir(const Grid& G, int d, const double* W, const double* slope, double* face) {
   long N = G.size, s = G.s[d];
   const double* qn[5];
@@ -475,7 +643,8 @@ static void interface_values_dir(const Grid& G, int d, const double* W, const do
     for (int j = lo[1]; j <= hi[1]; j++)
       for (int i = lo[0]; i <= hi[0]; i++) {
         long Z = G.at(i, j, k);
-        for (int m = 0; m < 5; m++) face[(long)m * N + Z] = interface_value(qn[m], slope + (long)m * N, Z, s);
+        for (int m = 0; m < 5; m++)
+          face[(long)m * N + Z] = slope ? interface_value(qn[m], slope + (long)m * N, Z, s) : cs_interface(qn[m], Z, s);
       }
 }
 
@@ -496,7 +665,7 @@ static void trace_zones_dir(const ob_box* b, const Grid& G, int d, double dt, do
       for (int i = -1; i <= G.n[0]; i++) {
         long Z = G.at(i, j, k);
         double qm[5], qp[5];
-        trace_zone(qn, fc, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, s, dtdx, qm, qp);
+        trace_zone(qn, fc, W + (long)W_C * N, W[(long)W_CHI * N + Z], Z, s, dtdx, b->limiter, qm, qp);
         for (int m = 0; m < 5; m++) {
           W[(long)(W_QM + 5 * d + m) * N + Z] = qm[m];
           W[(long)(W_QP + 5 * d + m) * N + Z] = qp[m];
@@ -508,8 +677,12 @@ static void trace_all(const ob_box* b, const Grid& G, double dt, double* W) {
   double* slope = (double*)calloc((size_t)5 * G.size, sizeof(double));
   double* face = (double*)calloc((size_t)5 * G.size, sizeof(double));
   for (int d = 0; d < 3; d++) {
-    limited_slopes_dir(G, d, W, slope);
-    interface_values_dir(G, d, W, slope, face);
+    if (b->limiter == 1) {
+      interface_values_dir(G, d, W, NULL, face);
+    } else {
+      limited_slopes_dir(G, d, W, slope);
+      interface_values_dir(G, d, W, slope, face);
+    }
     trace_zones_dir(b, G, d, dt, W, face);
   }
   free(slope);
@@ -537,7 +710,7 @@ static void normal_fluxes(const ob_box* b, const Grid& G, double* W) {
           double qL[5], qR[5], F[5];
           load_state(W, N, W_QP, d, Z - G.s[d], qL);
           load_state(W, N, W_QM, d, Z, qR);
-          hllc_xyz(d, qL, qR, b->gamma, F);
+          riemann_xyz(b->riemann, d, qL, qR, b->gamma, F);
           for (int v = 0; v < 5; v++) W[(long)(W_F0 + 5 * d + v) * N + Z] = F[v];
         }
   }
@@ -582,7 +755,7 @@ static void ctu_stage1(const ob_box* b, const Grid& G, double dt, double* W) {
             load_state(W, N, W_QM, d, Z, qR0);
             corrected_state(b, qL0, 1, &fac, &Fe, &se, ZL, N, qL);
             corrected_state(b, qR0, 1, &fac, &Fe, &se, Z, N, qR);
-            hllc_xyz(d, qL, qR, b->gamma, F);
+            riemann_xyz(b->riemann, d, qL, qR, b->gamma, F);
             for (int v = 0; v < 5; v++) out[v * N + Z] = F[v];
           }
     }
@@ -610,7 +783,7 @@ static void ctu_stage2(const ob_box* b, const Grid& G, double dt, double* W) {
           load_state(W, N, W_QM, d, Z, qR0);
           corrected_state(b, qL0, 2, fac, Fs, s, ZL, N, qL);
           corrected_state(b, qR0, 2, fac, Fs, s, Z, N, qR);
-          hllc_xyz(d, qL, qR, b->gamma, F);
+          riemann_xyz(b->riemann, d, qL, qR, b->gamma, F);
           /* R11: a reflecting face is impermeable -- no mass, energy or
            * tangential momentum crosses it, only the pressure force acts */
           int face = d == 0 ? i : (d == 1 ? j : k);
@@ -737,7 +910,26 @@ int oracle_run(const ob_box* b, double* U, int nsteps, double* dts, double* t, i
 
 /* HLLC flux across a face normal to d for x,y,z primitive states */
 void oracle_hllc(int d, const double* qL, const double* qR, double gamma, double* F) {
-  hllc_xyz(d, qL, qR, gamma, F);
+  riemann_xyz(0, d, qL, qR, gamma, F);
+}
+
+/* Two-shock solver on normal-frame states L, R = (rho, u_n, u_t1, u_t2, p):
+ * star pressure and velocity ps_us[2], the state at x/t = 0 (q[5]) and its
+ * flux (F[5]); returns the number of Newton steps. */
+int oracle_two_shock(const double* L, const double* R, double gamma, double* ps_us, double* q, double* F) {
+  int it = two_shock_star(L, R, gamma, &ps_us[0], &ps_us[1]);
+  two_shock_state(L, R, gamma, q);
+  euler_flux(q, gamma, F);
+  return it;
+}
+
+/* CS08 parabola of a 1D line a[n] with flattening chi[n]; zones 2..n-3 are written */
+void oracle_ppm_line_cs(const double* a, const double* chi, int n, double* aL, double* aR) {
+  for (long i = 2; i < n - 2; i++) {
+    aL[i] = cs_interface(a, i, 1);
+    aR[i] = cs_interface(a, i + 1, 1);
+    cs_limit_parabola(a, i, 1, chi[i], &aL[i], &aR[i]);
+  }
 }
 
 /* PPM parabola of a 1D line a[n] with flattening chi[n]; zones 2..n-3 are written */
@@ -771,7 +963,7 @@ void oracle_trace_line(const double* q, const double* c, const double* chi, int 
   }
   for (long i = 2; i < n - 2; i++) {
     double a[5], bq[5];
-    trace_zone(qn, fc, c, chi[i], i, 1, dtdx, a, bq);
+    trace_zone(qn, fc, c, chi[i], i, 1, dtdx, 0, a, bq);
     for (int m = 0; m < 5; m++) {
       qm[(long)m * n + i] = a[m];
       qp[(long)m * n + i] = bq[m];

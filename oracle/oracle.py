@@ -44,7 +44,12 @@ def build(force: bool = False) -> str:
 class ObBox(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("ng", ctypes.c_int), ("dx", ctypes.c_double * 3), ("gamma", ctypes.c_double),
-                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6)]
+                ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("limiter", ctypes.c_int),
+                ("riemann", ctypes.c_int)]
+
+# method variants: CW84 limiter (0) or Colella-Sekora (1); HLLC (0) or two-shock (1)
+LIMITER_CW84, LIMITER_CS08 = 0, 1
+RIEMANN_HLLC, RIEMANN_TWO_SHOCK = 0, 1
 
 
 _lib = None
@@ -75,6 +80,8 @@ def lib():
             L.oracle_limited_slope.restype = ctypes.c_double
             L.oracle_trace_line.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_double, _D, _D]
             L.oracle_flatten_line.argtypes = [_D, _D, ctypes.c_int, _D]
+            L.oracle_ppm_line_cs.argtypes = [_D, _D, ctypes.c_int, _D, _D]
+            L.oracle_two_shock.argtypes = [_D, _D, ctypes.c_double, _D, _D, _D]
             L.oracle_riemann_star.argtypes = [ctypes.c_double] * 7 + [_D, _D]
             L.oracle_riemann_sample.argtypes = [ctypes.c_double] * 7 + [_D, ctypes.c_int, _D, _D, _D]
             _lib = L
@@ -86,7 +93,7 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(_D)
 
 
-def make_box(shape, dx, gamma, cfl, bc, ng: int = NG) -> ObBox:
+def make_box(shape, dx, gamma, cfl, bc, ng: int = NG, limiter: int = 0, riemann: int = 0) -> ObBox:
     """shape = (nx, ny, nz); bc = six names (xlo, xhi, ylo, yhi, zlo, zhi)."""
     b = ObBox()
     b.nx, b.ny, b.nz = (int(v) for v in shape)
@@ -97,11 +104,14 @@ def make_box(shape, dx, gamma, cfl, bc, ng: int = NG) -> ObBox:
     b.cfl = float(cfl)
     for a in range(6):
         b.bc[a] = BC_CODES[bc[a]]
+    b.limiter = int(limiter)
+    b.riemann = int(riemann)
     return b
 
 
-def box_of(problem) -> ObBox:
-    return make_box(problem.shape, problem.dx, problem.gamma, problem.cfl, problem.bc)
+def box_of(problem, limiter: int = 0, riemann: int = 0) -> ObBox:
+    return make_box(problem.shape, problem.dx, problem.gamma, problem.cfl, problem.bc,
+                    limiter=limiter, riemann=riemann)
 
 
 def embed(U: np.ndarray, ng: int = NG) -> np.ndarray:
@@ -148,13 +158,14 @@ def step(box: ObBox, Ug: np.ndarray, dt: float, dump: bool = False, nthreads: in
     return rc, W
 
 
-def run(problem, nsteps: int | None = None, nthreads: int = 1):
-    """Advance `problem` nsteps (default problem.nsteps) with dt from the state.
+def run(problem, nsteps: int | None = None, nthreads: int = 1, limiter: int = 0, riemann: int = 0):
+    """Advance `problem` nsteps (default problem.nsteps) with dt from the state,
+    with the given limiter and Riemann solver.
 
     Returns (U_interior, t, dts, status).
     """
     n = problem.nsteps if nsteps is None else int(nsteps)
-    box = box_of(problem)
+    box = box_of(problem, limiter, riemann)
     Ug = embed(problem.U)
     dts = np.zeros(max(n, 1))
     t = ctypes.c_double()
@@ -179,6 +190,26 @@ def ppm_line(a, chi=None):
     aR = np.full_like(a, np.nan)
     lib().oracle_ppm_line(_p(a), _p(chi), a.size, _p(aL), _p(aR))
     return aL, aR
+
+
+def ppm_line_cs(a, chi=None):
+    """Colella-Sekora parabolas of a 1D line; zones 2..n-3 are written."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    chi = np.zeros_like(a) if chi is None else np.ascontiguousarray(chi, dtype=np.float64)
+    aL = np.full_like(a, np.nan)
+    aR = np.full_like(a, np.nan)
+    lib().oracle_ppm_line_cs(_p(a), _p(chi), a.size, _p(aL), _p(aR))
+    return aL, aR
+
+
+def two_shock(L, R, gamma: float):
+    """Two-shock solver on normal-frame states (rho, u_n, u_t1, u_t2, p).
+    Returns (p*, u*, interface state q[5], flux F[5], Newton steps)."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    pu, q, F = np.zeros(2), np.zeros(5), np.zeros(5)
+    it = lib().oracle_two_shock(_p(L), _p(R), float(gamma), _p(pu), _p(q), _p(F))
+    return pu[0], pu[1], q, F, it
 
 
 def limited_slope(am: float, a0: float, ap: float) -> float:

@@ -14,7 +14,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
-PIN_TESTS = ["tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_scheme.py"]
+PIN_TESTS = ["tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_scheme.py",
+             "tests/test_oracle_variants.py"]
+VARIANT_PINS_FIRST = PIN_TESTS[3:] + PIN_TESTS[:3]
 
 # (name, file, original text, planted mistake)
 MUTANTS = [
@@ -25,7 +27,7 @@ MUTANTS = [
     ("limited slope without the halving", "hydro_oracle.cpp",
      "double dc = 0.5 * (ap - am);", "double dc = (ap - am);"),
     ("flattening blend operands swapped", "hydro_oracle.cpp",
-     "*aL = f * a0 + (1.0 - f) * L;", "*aL = f * L + (1.0 - f) * a0;"),
+     "    }\n  }\n  *aL = f * a0 + (1.0 - f) * L;", "    }\n  }\n  *aL = f * L + (1.0 - f) * a0;"),
     ("tracing integral coefficient", "hydro_oracle.cpp",
      "return aR - 0.5 * sig * (dA - (1.0 - 2.0 * sig / 3.0) * a6);",
      "return aR - 0.5 * sig * (dA - (1.0 - sig / 3.0) * a6);"),
@@ -51,6 +53,31 @@ MUTANTS = [
      "double kin = 0.5 * rho * (u * u + v * v + w * w);", "double kin = 0.5 * rho * (u * u + v * v);"),
     ("exact solver shock function", "exact_riemann.cpp",
      "double root = sqrt(A / (p + B));", "double root = sqrt(A / (p - B));"),
+    ("CS08 interface weights", "hydro_oracle.cpp",
+     "- 1.0 / 12.0 * (am + a2);", "- 1.0 / 6.0 * (am + a2);"),
+    ("CS08 curvature bound constant", "hydro_oracle.cpp",
+     "static const double CS_C = 1.25;", "static const double CS_C = 1.0;"),
+    ("CS08 parabola curvature factor", "hydro_oracle.cpp",
+     "double d2 = 6.0 * (L + R - 2.0 * a0);", "double d2 = 3.0 * (L + R - 2.0 * a0);"),
+    ("CS08 interface curvature factor", "hydro_oracle.cpp",
+     "double d2 = 3.0 * (a0 - 2.0 * v + a1);", "double d2 = 6.0 * (a0 - 2.0 * v + a1);"),
+    ("CS08 extremum test needs both conditions", "hydro_oracle.cpp",
+     "if ((R - a0) * (a0 - L) <= 0.0 || (ap - a0) * (a0 - am) <= 0.0) {",
+     "if ((R - a0) * (a0 - L) <= 0.0 && (ap - a0) * (a0 - am) <= 0.0) {"),
+    ("CS08 edges not scaled", "hydro_oracle.cpp",
+     "L = a0 + (L - a0) * (lim / d2);", "L = a0 + (L - a0);"),
+    ("two-shock Hugoniot coefficients swapped", "hydro_oracle.cpp",
+     "0.5 * (gamma + 1.0) * ps + 0.5 * (gamma - 1.0) * p", "0.5 * (gamma - 1.0) * ps + 0.5 * (gamma + 1.0) * p"),
+    ("two-shock star density sign", "hydro_oracle.cpp",
+     "1.0 / (1.0 / rk - (ps - pk) / (Wk * Wk))", "1.0 / (1.0 / rk + (ps - pk) / (Wk * Wk))"),
+    ("two-shock samples the wrong side", "hydro_oracle.cpp",
+     "int left = us >= 0.0;", "int left = us < 0.0;"),
+    ("two-shock shock speed frame", "hydro_oracle.cpp",
+     "head = tail = Wk / rk - sgn * uk;", "head = tail = Wk / rk + sgn * uk;"),
+    ("two-shock fan weights swapped", "hydro_oracle.cpp",
+     "q[m] = (1.0 - a) * outer[m] + a * star[m];", "q[m] = a * outer[m] + (1.0 - a) * star[m];"),
+    ("two-shock fan tail uses the outer sound speed", "hydro_oracle.cpp",
+     "tail = sqrt(gamma * ps / rs) - sgn * us;", "tail = sqrt(gamma * pk / rk) - sgn * us;"),
 ]
 
 
@@ -74,8 +101,10 @@ def build_mutant(tmp, fname, old, new):
 def test_pins_catch_the_planted_mistake(name, fname, old, new):
     with tempfile.TemporaryDirectory() as tmp:
         lib = build_mutant(tmp, fname, old, new)
-        env = dict(os.environ, HYDRO_ORACLE_LIB=lib)
+        env = dict(os.environ, HYDRO_ORACLE_LIB=lib, OMP_WAIT_POLICY="passive")
+        # every pin file runs; the planted mistake's own area first, so that -x stops early
+        order = VARIANT_PINS_FIRST if name.startswith(("CS08", "two-shock")) else PIN_TESTS
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            "-m", "not slow", *PIN_TESTS], cwd=ROOT, env=env, capture_output=True,
+                            "-m", "not slow", *order], cwd=ROOT, env=env, capture_output=True,
                            text=True, timeout=600)
         assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
