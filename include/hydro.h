@@ -182,6 +182,30 @@ int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* of
 int hydro_set_neighbors(hydro_handle* h, const int32_t* neighbors);
 int hydro_set_shared_dt(hydro_handle* h, int enable);
 
+/* ---- method variants ----
+ * The paper says its hydro resembles Cholla's PPM scheme (§4) and prints no
+ * formulas; the default method is PPM with the Colella & Woodward (1984)
+ * limiter and an HLLC Riemann solver.  hydro_set_method selects, for every box
+ * of the handle:
+ *   limiter  HYDRO_LIMITER_CW84: van Leer slopes, 4th-order interfaces, CW84
+ *            monotonicity limiter (default);
+ *            HYDRO_LIMITER_CS08: Colella & Sekora (2008) extremum-preserving
+ *            limiter (4th-order interfaces limited through second differences,
+ *            smooth extrema kept unclipped, curvature bound C = 1.25);
+ *   riemann  HYDRO_RIEMANN_HLLC (default), or HYDRO_RIEMANN_TWO_SHOCK: the
+ *            two-shock approximation of Colella & Glaz (1985) (Newton on the
+ *            Hugoniot velocity balance from the acoustic guess, Hugoniot star
+ *            densities, linear interpolation across a rarefaction fan, Godunov
+ *            flux of the state at x/t = 0).
+ * Under HYDRO_LIMITER_CS08 the slope fields dq[3][5] of hydro_debug_fields
+ * hold instead the interface value at the low face of each zone.  Applies to
+ * the next step; HYDRO_ERR_INVALID on an unknown code. */
+#define HYDRO_LIMITER_CW84 0
+#define HYDRO_LIMITER_CS08 1
+#define HYDRO_RIEMANN_HLLC 0
+#define HYDRO_RIEMANN_TWO_SHOCK 1
+int hydro_set_method(hydro_handle* h, int limiter, int riemann);
+
 /* Launch configuration.  Every stage kernel covers all boxes of the handle in
  * one launch: the boxes' blocks are packed back to back through a work table
  * in the scratch head (block -> box and axis), so uneven boxes waste no

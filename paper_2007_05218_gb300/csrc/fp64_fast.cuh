@@ -68,6 +68,12 @@ __device__ __forceinline__ bool same_sign(R x, R y) {
   const auto a = dbits(x), b = dbits(y);
   return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
 }
+// x * y < 0: opposite signs and neither is zero
+template <typename R>
+__device__ __forceinline__ bool opp_sign(R x, R y) {
+  const auto a = dbits(x), b = dbits(y);
+  return (a ^ b) < 0 && (a << 1) != 0 && (b << 1) != 0;
+}
 // integer key that orders like the value (negatives flipped below positives)
 __device__ __forceinline__ long long dkey(double x) {
   const long long b = dbits(x);

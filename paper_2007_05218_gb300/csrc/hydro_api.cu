@@ -545,6 +545,18 @@ int hydro_set_shared_dt(hydro_handle* h, int enable) {
   return HYDRO_OK;
 }
 
+int hydro_set_method(hydro_handle* h, int limiter, int riemann) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  if (limiter != HYDRO_LIMITER_CW84 && limiter != HYDRO_LIMITER_CS08)
+    return fail(HYDRO_ERR_INVALID, "hydro_set_method: unknown limiter");
+  if (riemann != HYDRO_RIEMANN_HLLC && riemann != HYDRO_RIEMANN_TWO_SHOCK)
+    return fail(HYDRO_ERR_INVALID, "hydro_set_method: unknown Riemann solver");
+  h->plan.limiter = limiter;
+  h->plan.riemann = riemann;
+  drop_graph(h);
+  return HYDRO_OK;
+}
+
 int hydro_use_graphs(hydro_handle* h, int enable) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
   h->use_graphs = enable != 0;

@@ -133,6 +133,8 @@ struct Plan {
   long long max_ghosted, max_interior;
   WorkTable tab[NTABLES][2];  // [table][0: FP64 boxes (or all boxes), 1: mixed boxes]
   bool shared_dt = false;     // one dt for all boxes: the minimum of their CFL steps
+  int limiter = HYDRO_LIMITER_CW84;   // reconstruction variant of every box
+  int riemann = HYDRO_RIEMANN_HLLC;   // Riemann solver of every box
 };
 
 // Threads per block each table starts with (before any autotuning).

@@ -346,7 +346,82 @@ __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, 
   }
 }
 
+// ---------------------------------------- Colella & Sekora (2008) limiter
+// Curvature bound of CS08 (C = 1.25).
+constexpr double CS_C = 1.25;
+
+// CS08's limited second difference: when d2 and the neighbouring second
+// differences o[] all share a sign, the smallest of |d2| and C |o|, with the
+// sign of d2; else zero.
+template <typename R, int NO>
+__device__ __forceinline__ R cs_limited_d2(R d2, const R* o) {
+  R m = fabs(d2);
+#pragma unroll
+  for (int k = 0; k < NO; k++) {
+    if (!same_sign(d2, o[k])) return R(0);
+    m = dmin(m, R(CS_C) * fabs(o[k]));
+  }
+  return copysign(m, d2);
+}
+
+// Value at the face between zones a0 and a1 (neighbours am, a2): the
+// 4th-order interpolant, rebuilt from a limited second difference when it
+// does not lie between a0 and a1 (CS08 §2.1).
 template <typename R>
+__device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
+  R v = R(7.0 / 12.0) * (a0 + a1) - R(1.0 / 12.0) * (am + a2);
+  if (opp_sign(v - a0, a1 - v)) {
+    const R d2 = R(3) * (a0 - R(2) * v + a1);
+    const R o[2] = {am - R(2) * a0 + a1, a0 - R(2) * a1 + a2};
+    v = R(0.5) * (a0 + a1) - cs_limited_d2<R, 2>(d2, o) * R(1.0 / 6.0);
+  }
+  return v;
+}
+
+// Interface values of the five normal-frame variables of axis D at the low
+// face of each zone of [-2, n_D+1] along D and [-1, n] across it (stored in
+// the slope fields, which CS08 does not use).
+template <typename R, int D>
+__device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W, long long Z) {
+  const long long vs = b.vs, s = b.s[D];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    const R* a = W + comp<D>(m) * vs + Z;
+    W[(FLD_DQ + 5 * D + m) * vs + Z] = cs_interface(a[-2 * s], a[-s], a[0], a[s]);
+  }
+}
+
+// Parabola of zone value a0 (neighbours amm, am, ap, app) between the
+// interface values L, Rt: CS08's limiter (§2.2), then flattening by f.
+template <typename R>
+__device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt) {
+  if (!same_sign(Rt - a0, a0 - L) || !same_sign(ap - a0, a0 - am)) {
+    // an extremum in the zone or at a neighbour: keep the parabola's shape,
+    // its curvature limited by the second differences around it
+    const R d2 = R(6) * (L + Rt - R(2) * a0);
+    const R o[3] = {amm - R(2) * am + a0, am - R(2) * a0 + ap, a0 - R(2) * ap + app};
+    const R lim = cs_limited_d2<R, 3>(d2, o);
+    if (is_pos(fabs(lim))) {
+      const R sc = lim / d2;  // in (0, 1]; a true divide, as d2 may be subnormal
+      L = a0 + (L - a0) * sc;
+      Rt = a0 + (Rt - a0) * sc;
+    } else {
+      L = a0;
+      Rt = a0;
+    }
+  } else if (!dgt(R(2) * fabs(L - a0), fabs(Rt - a0))) {
+    Rt = a0 - R(2) * (L - a0);
+  } else if (!dgt(R(2) * fabs(Rt - a0), fabs(L - a0))) {
+    L = a0 - R(2) * (Rt - a0);
+  }
+  if (is_pos(f)) {
+    L = f * a0 + (R(1) - f) * L;
+    Rt = f * a0 + (R(1) - f) * Rt;
+  }
+}
+
+// Slope stage: van Leer slopes (CW84) or CS08 interface values, per zone.
+template <typename R, int LIM>
 __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __restrict__ boxes,
                                                 unsigned char* __restrict__ work) {
   LOCATE(tv)
@@ -358,10 +433,18 @@ __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __re
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
-  switch (d) {
-    case 0: slopes_zone<R, 0>(b, W, Z); break;
-    case 1: slopes_zone<R, 1>(b, W, Z); break;
-    default: slopes_zone<R, 2>(b, W, Z); break;
+  if constexpr (LIM == HYDRO_LIMITER_CS08) {
+    switch (d) {
+      case 0: cs_faces_zone<R, 0>(b, W, Z); break;
+      case 1: cs_faces_zone<R, 1>(b, W, Z); break;
+      default: cs_faces_zone<R, 2>(b, W, Z); break;
+    }
+  } else {
+    switch (d) {
+      case 0: slopes_zone<R, 0>(b, W, Z); break;
+      case 1: slopes_zone<R, 1>(b, W, Z); break;
+      default: slopes_zone<R, 2>(b, W, Z); break;
+    }
   }
 }
 
@@ -399,7 +482,7 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
   W[(base + 4 * D + 3) * vs + Z] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
-template <typename R, int D>
+template <typename R, int D, int LIM>
 __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
   const long long vs = b.vs, s = b.s[D];
   const R igm1 = Consts<R>::igm1(b);
@@ -410,7 +493,13 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
     const R* a = W + comp<D>(m) * vs + Z;
     const R* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
     a0[m] = a[0];
-    parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
+    if constexpr (LIM == HYDRO_LIMITER_CS08) {
+      aL[m] = dq[0];
+      aR[m] = dq[s];
+      cs_parabola(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
+    } else {
+      parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
+    }
   }
   R dA[5], a6[5];
 #pragma unroll
@@ -503,7 +592,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   store_conserved<R, D>(W, vs, Z, FLD_UM, out, igm1);
 }
 
-template <typename R>
+template <typename R, int LIM>
 __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __restrict__ boxes,
                                                const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   LOCATE(tv)
@@ -514,9 +603,9 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
   R* W = fields<R>(work, b);
   const BoxRt& r = rt[bi];
   switch (z_) {
-    case 0: trace_zone<R, 0>(b, W, Z, Consts<R>::dtdx(b, r, 0)); break;
-    case 1: trace_zone<R, 1>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
-    default: trace_zone<R, 2>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
+    case 0: trace_zone<R, 0, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 0)); break;
+    case 1: trace_zone<R, 1, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
+    default: trace_zone<R, 2, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
   }
 }
 
@@ -583,6 +672,101 @@ __device__ __forceinline__ void hllc(const R* L, R El, const R* Rs, R Er, R gamm
   F[3] = F[0] * wK;
 }
 
+// ------------------------------------------------- two-shock Riemann solver
+// Colella & Glaz (1985) two-shock approximation on normal-frame states
+// (rho, u_n, u_t1, u_t2, p) -> normal-frame Godunov flux.  Both nonlinear
+// waves follow their shock Hugoniot: across the wave of side K the velocity
+// changes by (p - p_K) / W_K(p), W_K^2 = rho_K ((gamma+1)/2 p + (gamma-1)/2 p_K).
+// p* solves the velocity balance by Newton's method from the acoustic guess
+// (floored at the pressure floor; stops when a step is at most TOL p*, at
+// most MAXIT steps), u* is the mean of the two sides' star velocities, the
+// star density follows the Hugoniot, 1/rho* = 1/rho_K - (p* - p_K)/W_K^2.
+// The state at x/t = 0 is taken on the side of the contact that holds it
+// (u* = 0: left), across a shock by its speed, across a rarefaction by
+// linear interpolation in x/t between head and tail.
+template <typename R>
+struct TwoShock;
+template <>
+struct TwoShock<double> {
+  static constexpr double TOL = 1e-12;
+  static constexpr int MAXIT = 40;
+};
+template <>
+struct TwoShock<float> {
+  static constexpr float TOL = 2e-6f;
+  static constexpr int MAXIT = 20;
+};
+
+template <typename R>
+__device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R igm1, R* F) {
+  const R rl = L[0], ul = L[1], pl = L[4];
+  const R rr = Rs[0], ur = Rs[1], pr = Rs[4];
+  const R hp = R(0.5) * (gamma + R(1)), hm = R(0.5) * (gamma - R(1));
+  const R al = rl * hp, bl = rl * hm * pl;  // W_L^2 = al p + bl
+  const R ar = rr * hp, br = rr * hm * pr;
+  const R Cl = nr_sqrt(gamma * pl * rl), Cr = nr_sqrt(gamma * pr * rr);  // acoustic impedances
+  R p = (Cr * pl + Cl * pr + Cl * Cr * (ul - ur)) * nr_rcp(Cl + Cr);
+  p = dmax(p, R(SMALL_PRES));
+  for (int it = 0; it < TwoShock<R>::MAXIT; it++) {
+    const R iwl = nr_rsqrt(al * p + bl), iwr = nr_rsqrt(ar * p + br);  // 1 / W
+    const R dpl = p - pl, dpr = p - pr;
+    const R f = dpl * iwl + dpr * iwr + (ur - ul);
+    // d/dp (p - p_K) / W_K = (1 - (p - p_K) (a_K / 2) / W_K^2) / W_K
+    const R dl = (R(1) - dpl * (R(0.5) * al) * iwl * iwl) * iwl;
+    const R dr = (R(1) - dpr * (R(0.5) * ar) * iwr * iwr) * iwr;
+    const R pn = dmax(p - f * nr_rcp(dl + dr), R(SMALL_PRES));
+    const R step = fabs(pn - p);
+    p = pn;
+    if (!dgt(step, R(TwoShock<R>::TOL) * p)) break;
+  }
+  const R iwl = nr_rsqrt(al * p + bl), iwr = nr_rsqrt(ar * p + br);
+  const R us = R(0.5) * ((ul - (p - pl) * iwl) + (ur + (p - pr) * iwr));
+  const bool left = is_nonneg(us);
+  const R rk = left ? rl : rr, uk = left ? ul : ur, pk = left ? pl : pr;
+  const R vk = left ? L[2] : Rs[2], wk = left ? L[3] : Rs[3];
+  const R iwk = left ? iwl : iwr, w2k = left ? al * p + bl : ar * p + br;
+  const R sgn = left ? R(1) : R(-1);  // the side's wave moves with u - sgn c
+  const R irk = nr_rcp(rk);
+  const R irs = irk - (p - pk) * iwk * iwk;  // 1 / rho*
+  // speeds of the side's wave head and tail relative to x/t = 0, positive
+  // while they are on the side's own half
+  R head, tail;
+  if (dgt(p, pk)) {
+    head = w2k * iwk * irk - sgn * uk;  // shock: |S - u_K| = W_K / rho_K
+    tail = head;
+  } else {
+    const R gpk = gamma * pk * irk, gps = gamma * p * irs;
+    head = gpk * nr_rsqrt(gpk) - sgn * uk;
+    tail = gps * nr_rsqrt(gps) - sgn * us;
+  }
+  R q0, q1, q4;
+  if (!is_pos(head)) {
+    q0 = rk; q1 = uk; q4 = pk;            // the wave has left x/t = 0 behind
+  } else if (is_nonneg(tail)) {
+    q0 = nr_rcp(irs); q1 = us; q4 = p;    // star state
+  } else {
+    const R a = head * nr_rcp(head - tail);  // x/t = 0 inside the fan
+    q0 = (R(1) - a) * rk + a * nr_rcp(irs);
+    q1 = (R(1) - a) * uk + a * us;
+    q4 = (R(1) - a) * pk + a * p;
+  }
+  const R mu = q0 * q1;
+  const R E = q4 * igm1 + R(0.5) * q0 * (q1 * q1 + vk * vk + wk * wk);
+  F[0] = mu;
+  F[1] = mu * q1 + q4;
+  F[2] = mu * vk;
+  F[3] = mu * wk;
+  F[4] = (E + q4) * q1;
+}
+
+// The handle's Riemann solver.  El, Er: total energies of the states (HLLC
+// uses them; the two-shock flux is built from the sampled state alone).
+template <typename R, int RS>
+__device__ __forceinline__ void riemann(const R* L, R El, const R* Rs, R Er, R gamma, R igm1, R* F) {
+  if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock(L, Rs, gamma, igm1, F);
+  else hllc(L, El, Rs, Er, gamma, F);
+}
+
 // The two states of the D-face at zone Z: primitive q (5) and conserved
 // momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides.
 template <typename R, int D>
@@ -606,15 +790,15 @@ __device__ __forceinline__ void store_flux(R* __restrict__ dst, long long vs, lo
   for (int m = 0; m < 5; m++) dst[comp<D>(m) * vs + Z] = Fn[m];
 }
 
-template <typename R, int D>
+template <typename R, int D, int RS>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, uL, qR, uR);
-  hllc(qL, uL[3], qR, uR[3], Consts<R>::gamma(b), Fn);
+  riemann<R, RS>(qL, uL[3], qR, uR[3], Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
-template <typename R>
+template <typename R, int RS>
 __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __restrict__ boxes,
                                                  unsigned char* __restrict__ work) {
   LOCATE(tv)
@@ -627,9 +811,9 @@ __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __r
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   switch (d) {
-    case 0: riemann_face<R, 0>(b, W, Z); break;
-    case 1: riemann_face<R, 1>(b, W, Z); break;
-    default: riemann_face<R, 2>(b, W, Z); break;
+    case 0: riemann_face<R, 0, RS>(b, W, Z); break;
+    case 1: riemann_face<R, 1, RS>(b, W, Z); break;
+    default: riemann_face<R, 2, RS>(b, W, Z); break;
   }
 }
 
@@ -671,7 +855,7 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
 
-template <typename R, int D, int E>
+template <typename R, int D, int E, int RS>
 __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt) {
   const long long vs = b.vs, sD = b.s[D];
   const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
@@ -682,11 +866,11 @@ __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, lo
   const R fac[1] = {Consts<R>::dtdx(b, rt, E) * R(1.0 / 3.0)};
   const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
   const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
-  hllc(qL, EL, qR, ER, gamma, Fn);
+  riemann<R, RS>(qL, EL, qR, ER, gamma, igm1, Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
 }
 
-template <typename R>
+template <typename R, int RS>
 __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __restrict__ boxes,
                                               const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   LOCATE(tv)
@@ -704,16 +888,16 @@ __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __rest
   R* W = fields<R>(work, b);
   const BoxRt& rtb = rt[bi];
   switch (p) {
-    case 0: ctu1_face<R, 0, 1>(b, W, Z, rtb); break;
-    case 1: ctu1_face<R, 0, 2>(b, W, Z, rtb); break;
-    case 2: ctu1_face<R, 1, 0>(b, W, Z, rtb); break;
-    case 3: ctu1_face<R, 1, 2>(b, W, Z, rtb); break;
-    case 4: ctu1_face<R, 2, 0>(b, W, Z, rtb); break;
-    default: ctu1_face<R, 2, 1>(b, W, Z, rtb); break;
+    case 0: ctu1_face<R, 0, 1, RS>(b, W, Z, rtb); break;
+    case 1: ctu1_face<R, 0, 2, RS>(b, W, Z, rtb); break;
+    case 2: ctu1_face<R, 1, 0, RS>(b, W, Z, rtb); break;
+    case 3: ctu1_face<R, 1, 2, RS>(b, W, Z, rtb); break;
+    case 4: ctu1_face<R, 2, 0, RS>(b, W, Z, rtb); break;
+    default: ctu1_face<R, 2, 1, RS>(b, W, Z, rtb); break;
   }
 }
 
-template <typename R, int D>
+template <typename R, int D, int RS>
 __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
                                           bool wall) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
@@ -726,7 +910,7 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
   const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
   const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
-  hllc(qL, EL, qR, ER, gamma, Fn);
+  riemann<R, RS>(qL, EL, qR, ER, gamma, igm1, Fn);
   if (wall) {
     // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
     Fn[0] = R(0);
@@ -737,7 +921,7 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   store_flux<R, D>(W + (FLD_F + 5 * D) * vs, vs, Z, Fn);
 }
 
-template <typename R>
+template <typename R, int RS>
 __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __restrict__ boxes,
                                               const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   LOCATE(tv)
@@ -752,9 +936,9 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
   const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT && b.nbr1[2 * d] == 0) ||
                     (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * d + 1] == 0);
   switch (d) {
-    case 0: ctu2_face<R, 0>(b, W, Z, r, wall); break;
-    case 1: ctu2_face<R, 1>(b, W, Z, r, wall); break;
-    default: ctu2_face<R, 2>(b, W, Z, r, wall); break;
+    case 0: ctu2_face<R, 0, RS>(b, W, Z, r, wall); break;
+    case 1: ctu2_face<R, 1, RS>(b, W, Z, r, wall); break;
+    default: ctu2_face<R, 2, RS>(b, W, Z, r, wall); break;
   }
 }
 
@@ -920,6 +1104,39 @@ int launch(void (*k)(TableView, A...), const WorkTable& w, cudaStream_t s, P... 
   return 1;
 }
 
+// Launches the compute-type-R kernel of a per-precision table over w with the
+// handle's method variant; returns 1 if it had work.
+template <typename R>
+int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
+  const BoxRt* rt = p.rt;
+  const bool cs = p.limiter == HYDRO_LIMITER_CS08;
+  const bool ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
+  switch (table) {
+    case TB_FLATTEN: return launch(k_flatten<R>, w, s, p.dboxes, p.work);
+    case TB_SLOPES:
+      return cs ? launch(k_slopes<R, HYDRO_LIMITER_CS08>, w, s, p.dboxes, p.work)
+                : launch(k_slopes<R, HYDRO_LIMITER_CW84>, w, s, p.dboxes, p.work);
+    case TB_TRACE:
+      return cs ? launch(k_trace<R, HYDRO_LIMITER_CS08>, w, s, p.dboxes, rt, p.work)
+                : launch(k_trace<R, HYDRO_LIMITER_CW84>, w, s, p.dboxes, rt, p.work);
+    case TB_RIEMANN:
+      return ts ? launch(k_riemann<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, p.work)
+                : launch(k_riemann<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, p.work);
+    case TB_CTU1:
+      return ts ? launch(k_ctu1<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                : launch(k_ctu1<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    case TB_CTU2:
+      return ts ? launch(k_ctu2<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                : launch(k_ctu2<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    default: return 0;
+  }
+}
+
+// Both compute types of a per-precision table.
+int launch_both(const Plan& p, int table, cudaStream_t s) {
+  return launch_typed<double>(p, table, p.tab[table][0], s) + launch_typed<float>(p, table, p.tab[table][1], s);
+}
+
 }  // namespace
 
 cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const double* dt_in, double* dt_out,
@@ -942,30 +1159,12 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
         k_dt<<<(p.nboxes + 255) / 256, 256, 0, stream>>>(p.dboxes, p.rt, p.nboxes, dt_in, dt_out, advance);
       n = 1;
       break;
-    case ST_FLATTEN:
-      n += launch(k_flatten<double>, T[TB_FLATTEN][0], stream, p.dboxes, p.work);
-      n += launch(k_flatten<float>, T[TB_FLATTEN][1], stream, p.dboxes, p.work);
-      break;
-    case ST_SLOPES:
-      n += launch(k_slopes<double>, T[TB_SLOPES][0], stream, p.dboxes, p.work);
-      n += launch(k_slopes<float>, T[TB_SLOPES][1], stream, p.dboxes, p.work);
-      break;
-    case ST_TRACE:
-      n += launch(k_trace<double>, T[TB_TRACE][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      n += launch(k_trace<float>, T[TB_TRACE][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      break;
-    case ST_RIEMANN:
-      n += launch(k_riemann<double>, T[TB_RIEMANN][0], stream, p.dboxes, p.work);
-      n += launch(k_riemann<float>, T[TB_RIEMANN][1], stream, p.dboxes, p.work);
-      break;
-    case ST_CTU1:
-      n += launch(k_ctu1<double>, T[TB_CTU1][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      n += launch(k_ctu1<float>, T[TB_CTU1][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      break;
-    case ST_CTU2:
-      n += launch(k_ctu2<double>, T[TB_CTU2][0], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      n += launch(k_ctu2<float>, T[TB_CTU2][1], stream, p.dboxes, (const BoxRt*)p.rt, p.work);
-      break;
+    case ST_FLATTEN: n += launch_both(p, TB_FLATTEN, stream); break;
+    case ST_SLOPES: n += launch_both(p, TB_SLOPES, stream); break;
+    case ST_TRACE: n += launch_both(p, TB_TRACE, stream); break;
+    case ST_RIEMANN: n += launch_both(p, TB_RIEMANN, stream); break;
+    case ST_CTU1: n += launch_both(p, TB_CTU1, stream); break;
+    case ST_CTU2: n += launch_both(p, TB_CTU2, stream); break;
     case ST_UPDATE:
       n += launch(k_update, T[TB_UPDATE][0], stream, p.dboxes, p.rt, p.state, p.work);
       break;
@@ -978,35 +1177,19 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
 
 cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream) {
   const WorkTable& w = p.tab[table][slot];
-  const BoxRt* rt = p.rt;
   switch (table) {
     case TB_FILL_X: launch(k_fill<0>, w, stream, p.dboxes, p.state); break;
     case TB_FILL_Y: launch(k_fill<1>, w, stream, p.dboxes, p.state); break;
     case TB_FILL_Z: launch(k_fill<2>, w, stream, p.dboxes, p.state); break;
     case TB_PRIM: launch(k_prim, w, stream, p.dboxes, (const double*)p.state, p.work, p.rt); break;
     case TB_FLATTEN:
-      if (slot == 0) launch(k_flatten<double>, w, stream, p.dboxes, p.work);
-      else launch(k_flatten<float>, w, stream, p.dboxes, p.work);
-      break;
     case TB_SLOPES:
-      if (slot == 0) launch(k_slopes<double>, w, stream, p.dboxes, p.work);
-      else launch(k_slopes<float>, w, stream, p.dboxes, p.work);
-      break;
     case TB_TRACE:
-      if (slot == 0) launch(k_trace<double>, w, stream, p.dboxes, rt, p.work);
-      else launch(k_trace<float>, w, stream, p.dboxes, rt, p.work);
-      break;
     case TB_RIEMANN:
-      if (slot == 0) launch(k_riemann<double>, w, stream, p.dboxes, p.work);
-      else launch(k_riemann<float>, w, stream, p.dboxes, p.work);
-      break;
     case TB_CTU1:
-      if (slot == 0) launch(k_ctu1<double>, w, stream, p.dboxes, rt, p.work);
-      else launch(k_ctu1<float>, w, stream, p.dboxes, rt, p.work);
-      break;
     case TB_CTU2:
-      if (slot == 0) launch(k_ctu2<double>, w, stream, p.dboxes, rt, p.work);
-      else launch(k_ctu2<float>, w, stream, p.dboxes, rt, p.work);
+      if (slot == 0) launch_typed<double>(p, table, w, stream);
+      else launch_typed<float>(p, table, w, stream);
       break;
     default:
       return cudaErrorInvalidValue;  // the update changes the state and is not relaunched

@@ -28,13 +28,16 @@ HYDRO_BC = {"periodic": 0, "outflow": 1, "reflect": 2}
 HYDRO_FP64 = 0
 HYDRO_MIXED = 1
 HYDRO_NG = 4
+HYDRO_LIMITER_CW84, HYDRO_LIMITER_CS08 = 0, 1
+HYDRO_RIEMANN_HLLC, HYDRO_RIEMANN_TWO_SHOCK = 0, 1
 
 EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_free", "hydro_fill_ghosts",
             "hydro_compute_dt", "hydro_step", "hydro_sync", "hydro_get_time", "hydro_upload",
             "hydro_download", "hydro_debug_fields", "hydro_kernel_launches", "hydro_profile_begin",
             "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
             "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
-            "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_last_error")
+            "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_set_method",
+            "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -122,6 +125,7 @@ def load(path: str | None = None):
         L.hydro_use_graphs.argtypes = [_VP, i]
         L.hydro_set_neighbors.argtypes = [_VP, _VP]
         L.hydro_set_shared_dt.argtypes = [_VP, i]
+        L.hydro_set_method.argtypes = [_VP, i, i]
         L.hydro_server_create.argtypes = [ctypes.POINTER(hydro_server_config), ctypes.POINTER(_VP)]
         L.hydro_server_destroy.argtypes = [_VP]
         L.hydro_submit.argtypes = [_VP, ctypes.POINTER(hydro_request), ctypes.POINTER(ctypes.c_int64)]
@@ -286,6 +290,11 @@ def hydro_set_shared_dt(h: int, enable: bool) -> None:
     _check(load().hydro_set_shared_dt(h, int(bool(enable))))
 
 
+def hydro_set_method(h: int, limiter: int = 0, riemann: int = 0) -> None:
+    """limiter: HYDRO_LIMITER_CW84 / HYDRO_LIMITER_CS08; riemann: HYDRO_RIEMANN_HLLC / HYDRO_RIEMANN_TWO_SHOCK."""
+    _check(load().hydro_set_method(h, int(limiter), int(riemann)))
+
+
 def hydro_use_graphs(h: int, enable: bool) -> None:
     _check(load().hydro_use_graphs(h, int(bool(enable))))
 
@@ -379,7 +388,7 @@ class Server:
 class Boxes:
     """Owns torch-allocated state and scratch for a set of boxes and a handle."""
 
-    def __init__(self, problems_or_descs, device="cuda", precision=HYDRO_FP64):
+    def __init__(self, problems_or_descs, device="cuda", precision=HYDRO_FP64, limiter=0, riemann=0):
         import torch
         items = list(problems_or_descs)
         self.descs = [p if isinstance(p, hydro_box_desc) else desc_of(p, precision) for p in items]
@@ -390,6 +399,8 @@ class Boxes:
         self.scratch = torch.empty((wb + 7) // 8, dtype=torch.float64, device=device)
         self.layouts = [hydro_box_layout(self.descs, b) for b in range(self.nboxes)]
         self.h = hydro_alloc(self.descs, self.state, sb, self.scratch, wb)
+        if limiter or riemann:
+            hydro_set_method(self.h, limiter, riemann)
         self.dt = torch.zeros(self.nboxes, dtype=torch.float64, device=device)
         for k, p in enumerate(items):
             if not isinstance(p, hydro_box_desc):

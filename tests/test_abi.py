@@ -38,6 +38,20 @@ def test_library_exports_every_declared_symbol():
     assert set(hydro.EXPORTED) <= set(declared_functions())
 
 
+def test_binding_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "hydro.h")).read()
+    defs = dict(re.findall(r"^#define (HYDRO_\w+) \(?(-?\d+)\)?", text, flags=re.M))
+    mirrored = [n for n in defs if hasattr(hydro, n)]
+    assert {"HYDRO_LIMITER_CS08", "HYDRO_RIEMANN_TWO_SHOCK", "HYDRO_MIXED", "HYDRO_NG"} <= set(mirrored)
+    for n in mirrored:
+        assert getattr(hydro, n) == int(defs[n]), n
+
+
+def test_method_selection_rejects_a_null_handle():
+    with pytest.raises(hydro.HydroError):
+        hydro.hydro_set_method(None, hydro.HYDRO_LIMITER_CS08, hydro.HYDRO_RIEMANN_HLLC)
+
+
 def test_workspace_and_layout_planning():
     pr = inputs.density_wave((20, 12, 9), noise=0.0)
     d = hydro.desc_of(pr)
