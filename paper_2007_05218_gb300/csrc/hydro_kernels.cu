@@ -168,6 +168,13 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
 // ------------------------------------------------- conserved -> primitive, dt
 // FP64 arithmetic for every box (the dt reduction needs it); the primitive
 // fields are stored in the box's compute type.
+// EXACT (used under the CS08 limiter, whose branches are not continuous in
+// their inputs): the primitive state with correctly rounded divides and square
+// root and no fused multiply-adds, u = U1 / rho, ..., p = (gamma - 1)(E -
+// (rho / 2)(u^2 + v^2 + w^2)), c = sqrt(gamma p / rho), in that order, so that
+// the limiter's decisions are reproducible on any IEEE machine.  Otherwise one
+// approximate reciprocal and square root.
+template <bool EXACT>
 __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes,
                                               const double* __restrict__ state, unsigned char* __restrict__ work,
                                               BoxRt* __restrict__ rt) {
@@ -182,11 +189,25 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
     const double* U = state + b.state_off;
     double rho = U[Z];
     if (rho < SMALL_DENS) rho = SMALL_DENS;
-    const double ir = nr_rcp(rho);
-    const double u = U[vs + Z] * ir, v = U[2 * vs + Z] * ir, w = U[3 * vs + Z] * ir;
-    double p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
-    if (p < SMALL_PRES) p = SMALL_PRES;
-    const double cs = nr_sqrt(b.gamma * p * ir);
+    double u, v, w, p, cs;
+    if constexpr (EXACT) {
+      u = __ddiv_rn(U[vs + Z], rho);
+      v = __ddiv_rn(U[2 * vs + Z], rho);
+      w = __ddiv_rn(U[3 * vs + Z], rho);
+      const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+      const double kin = __dmul_rn(__dmul_rn(0.5, rho), uu);
+      p = __dmul_rn(__dsub_rn(b.gamma, 1.0), __dsub_rn(U[4 * vs + Z], kin));
+      if (p < SMALL_PRES) p = SMALL_PRES;
+      cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(b.gamma, p), rho));
+    } else {
+      const double ir = nr_rcp(rho);
+      u = U[vs + Z] * ir;
+      v = U[2 * vs + Z] * ir;
+      w = U[3 * vs + Z] * ir;
+      p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
+      if (p < SMALL_PRES) p = SMALL_PRES;
+      cs = nr_sqrt(b.gamma * p * ir);
+    }
     if (b.precision == HYDRO_FP64) {
       double* W = fields<double>(work, b);
       W[Z] = rho;
@@ -350,6 +371,26 @@ __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, 
 // Curvature bound of CS08 (C = 1.25).
 constexpr double CS_C = 1.25;
 
+// CS08's branches (interface in bounds, zone or neighbour at an extremum,
+// second differences of one sign) are not continuous in their inputs: a
+// one-ulp change can move an edge value by the size of the limited
+// curvature.  So every quantity a branch depends on is formed with single
+// IEEE operations (no contraction into fused multiply-adds) in the order the
+// method writes them, and equal inputs give bitwise equal decisions and
+// edges on any IEEE machine.
+__device__ __forceinline__ double ie_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ie_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ie_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ie_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float ie_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ie_div(float a, float b) { return __fdiv_rn(a, b); }
+
+// second difference a - 2 b + c, as (a - 2 b) + c
+template <typename R>
+__device__ __forceinline__ R ie_d2(R a, R b, R c) { return ie_add(ie_sub(a, ie_mul(R(2), b)), c); }
+
 // CS08's limited second difference: when d2 and the neighbouring second
 // differences o[] all share a sign, the smallest of |d2| and C |o|, with the
 // sign of d2; else zero.
@@ -359,21 +400,22 @@ __device__ __forceinline__ R cs_limited_d2(R d2, const R* o) {
 #pragma unroll
   for (int k = 0; k < NO; k++) {
     if (!same_sign(d2, o[k])) return R(0);
-    m = dmin(m, R(CS_C) * fabs(o[k]));
+    m = dmin(m, ie_mul(R(CS_C), fabs(o[k])));
   }
   return copysign(m, d2);
 }
 
 // Value at the face between zones a0 and a1 (neighbours am, a2): the
-// 4th-order interpolant, rebuilt from a limited second difference when it
-// does not lie between a0 and a1 (CS08 §2.1).
+// 4th-order interpolant 7/12 (a0 + a1) - 1/12 (am + a2), rebuilt as
+// (a0 + a1)/2 - d2_lim/6 from the limited second difference d2 = 3 (a0 - 2v + a1)
+// when it does not lie between a0 and a1 (CS08 §2.1).
 template <typename R>
 __device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
-  R v = R(7.0 / 12.0) * (a0 + a1) - R(1.0 / 12.0) * (am + a2);
-  if (opp_sign(v - a0, a1 - v)) {
-    const R d2 = R(3) * (a0 - R(2) * v + a1);
-    const R o[2] = {am - R(2) * a0 + a1, a0 - R(2) * a1 + a2};
-    v = R(0.5) * (a0 + a1) - cs_limited_d2<R, 2>(d2, o) * R(1.0 / 6.0);
+  R v = ie_sub(ie_mul(R(7.0 / 12.0), ie_add(a0, a1)), ie_mul(R(1.0 / 12.0), ie_add(am, a2)));
+  if (opp_sign(ie_sub(v, a0), ie_sub(a1, v))) {
+    const R d2 = ie_mul(R(3), ie_add(ie_sub(a0, ie_mul(R(2), v)), a1));
+    const R o[2] = {ie_d2(am, a0, a1), ie_d2(a0, a1, a2)};
+    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_div(cs_limited_d2<R, 2>(d2, o), R(6)));
   }
   return v;
 }
@@ -392,31 +434,34 @@ __device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W
 }
 
 // Parabola of zone value a0 (neighbours amm, am, ap, app) between the
-// interface values L, Rt: CS08's limiter (§2.2), then flattening by f.
+// interface values L, Rt: CS08's limiter (§2.2) -- at an extremum of the zone
+// or of a neighbour the parabola keeps its shape with its curvature
+// 6 (L + Rt - 2 a0) limited by the neighbouring second differences, else the
+// CW84 overshoot rule -- then flattening by f.  Single IEEE operations, as
+// for cs_interface.
 template <typename R>
 __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt) {
-  if (!same_sign(Rt - a0, a0 - L) || !same_sign(ap - a0, a0 - am)) {
-    // an extremum in the zone or at a neighbour: keep the parabola's shape,
-    // its curvature limited by the second differences around it
-    const R d2 = R(6) * (L + Rt - R(2) * a0);
-    const R o[3] = {amm - R(2) * am + a0, am - R(2) * a0 + ap, a0 - R(2) * ap + app};
+  if (!same_sign(ie_sub(Rt, a0), ie_sub(a0, L)) || !same_sign(ie_sub(ap, a0), ie_sub(a0, am))) {
+    const R d2 = ie_mul(R(6), ie_sub(ie_add(L, Rt), ie_mul(R(2), a0)));
+    const R o[3] = {ie_d2(amm, am, a0), ie_d2(am, a0, ap), ie_d2(a0, ap, app)};
     const R lim = cs_limited_d2<R, 3>(d2, o);
     if (is_pos(fabs(lim))) {
-      const R sc = lim / d2;  // in (0, 1]; a true divide, as d2 may be subnormal
-      L = a0 + (L - a0) * sc;
-      Rt = a0 + (Rt - a0) * sc;
+      const R sc = ie_div(lim, d2);  // in (0, 1]
+      L = ie_add(a0, ie_mul(ie_sub(L, a0), sc));
+      Rt = ie_add(a0, ie_mul(ie_sub(Rt, a0), sc));
     } else {
       L = a0;
       Rt = a0;
     }
-  } else if (!dgt(R(2) * fabs(L - a0), fabs(Rt - a0))) {
-    Rt = a0 - R(2) * (L - a0);
-  } else if (!dgt(R(2) * fabs(Rt - a0), fabs(L - a0))) {
-    L = a0 - R(2) * (Rt - a0);
+  } else if (!dgt(ie_mul(R(2), fabs(ie_sub(L, a0))), fabs(ie_sub(Rt, a0)))) {
+    Rt = ie_sub(a0, ie_mul(R(2), ie_sub(L, a0)));
+  } else if (!dgt(ie_mul(R(2), fabs(ie_sub(Rt, a0))), fabs(ie_sub(L, a0)))) {
+    L = ie_sub(a0, ie_mul(R(2), ie_sub(Rt, a0)));
   }
   if (is_pos(f)) {
-    L = f * a0 + (R(1) - f) * L;
-    Rt = f * a0 + (R(1) - f) * Rt;
+    const R g = ie_sub(R(1), f);
+    L = ie_add(ie_mul(f, a0), ie_mul(g, L));
+    Rt = ie_add(ie_mul(f, a0), ie_mul(g, Rt));
   }
 }
 
@@ -1150,7 +1195,10 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
       n += launch(k_fill<2>, T[TB_FILL_Z][0], stream, p.dboxes, p.state);
       break;
     case ST_PRIM:
-      n += launch(k_prim, T[TB_PRIM][0], stream, p.dboxes, (const double*)p.state, p.work, p.rt);
+      if (p.limiter == HYDRO_LIMITER_CS08)
+        n += launch(k_prim<true>, T[TB_PRIM][0], stream, p.dboxes, (const double*)p.state, p.work, p.rt);
+      else
+        n += launch(k_prim<false>, T[TB_PRIM][0], stream, p.dboxes, (const double*)p.state, p.work, p.rt);
       break;
     case ST_DT:
       if (p.shared_dt && !dt_in)
@@ -1181,7 +1229,10 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
     case TB_FILL_X: launch(k_fill<0>, w, stream, p.dboxes, p.state); break;
     case TB_FILL_Y: launch(k_fill<1>, w, stream, p.dboxes, p.state); break;
     case TB_FILL_Z: launch(k_fill<2>, w, stream, p.dboxes, p.state); break;
-    case TB_PRIM: launch(k_prim, w, stream, p.dboxes, (const double*)p.state, p.work, p.rt); break;
+    case TB_PRIM:
+      if (p.limiter == HYDRO_LIMITER_CS08) launch(k_prim<true>, w, stream, p.dboxes, (const double*)p.state, p.work, p.rt);
+      else launch(k_prim<false>, w, stream, p.dboxes, (const double*)p.state, p.work, p.rt);
+      break;
     case TB_FLATTEN:
     case TB_SLOPES:
     case TB_TRACE:
