@@ -224,6 +224,37 @@ def run_batched(hydro, inputs, torch, np, stream, nboxes=512, nsteps=30):
 
 
 # ------------------------------------------------------------ served stream
+def run_variants(hydro, torch, pr, stream, warmup, nsteps=20):
+    """The method variants on the same box, FP64: Colella-Sekora limiter,
+    two-shock Riemann solver, both.  W warm-up steps, then nsteps timed with
+    events on the launching stream; per-stage event times per step."""
+    out = {}
+    N = pr.U[0].size
+    for name, lim, rs in (("cs08", hydro.HYDRO_LIMITER_CS08, hydro.HYDRO_RIEMANN_HLLC),
+                          ("two_shock", hydro.HYDRO_LIMITER_CW84, hydro.HYDRO_RIEMANN_TWO_SHOCK),
+                          ("cs08_two_shock", hydro.HYDRO_LIMITER_CS08, hydro.HYDRO_RIEMANN_TWO_SHOCK)):
+        V = hydro.Boxes([pr], limiter=lim, riemann=rs)
+        V.step(warmup)
+        V.sync()
+        torch.cuda.synchronize()
+        hydro.hydro_profile_begin(V.h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nsteps):
+            hydro.hydro_step(V.h, None, 1, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = hydro.hydro_profile_end(V.h)
+        V.sync()
+        V.close()
+        out[name] = {"value": N * nsteps / (ms * 1e-3), "unit": UNIT, "steps": nsteps,
+                     "ms_per_step": ms / nsteps,
+                     "stages_ms_per_step": {k: v[1] / nsteps for k, v in prof.items()}}
+    return out
+
+
 def run_served(hydro, inputs, torch, np, nrequests, budget_gb=120.0, max_active=256):
     """Continuous batching of a seeded request stream (Poisson arrivals at
     200/s, box edges uniform in [32,128], 10-200 steps, Sod/Sedov/shear-layer
@@ -286,6 +317,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-box batched measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the limiter / Riemann variant measurement")
     ap.add_argument("--served-requests", type=int, default=48,
                     help="length of the served request stream (0 skips it; the full stream is 2000)")
     ap.add_argument("--box", type=int, default=N_BOX, help="box edge (default 256; smaller only for profiling)")
@@ -399,6 +431,7 @@ def main() -> None:
     del M
     rel_l1 = {name: float(np.abs(mixed_final[v] - fp64_final[v]).sum() / np.abs(fp64_final[v]).sum())
               for name, v in (("rho", 0), ("E", 4))}
+    variants = None if args.no_variants else run_variants(hydro, torch, pr, stream, args.warmup)
     batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
     served = run_served(hydro, inputs, torch, np, args.served_requests) if args.served_requests > 0 else None
     mixed = {"value": world * N * args.steps / (ms_mixed * 1e-3), "unit": UNIT,
@@ -447,6 +480,7 @@ def main() -> None:
         "cpu_baseline": cpu,
         "e2e": e2e,
         "mixed": mixed,
+        "variants": variants,
         "batched": batched,
         "served": served,
         "gpu_launches": launches,

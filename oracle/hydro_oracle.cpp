@@ -306,7 +306,7 @@ static double cs_interface(const double* a, long Z, long s) {
   if ((v - a0) * (a1 - v) < 0.0) {
     double d2 = 3.0 * (a0 - 2.0 * v + a1);
     double nb[2] = {am - 2.0 * a0 + a1, a0 - 2.0 * a1 + a2};
-    v = 0.5 * (a0 + a1) - cs_limited_d2(d2, nb, 2) / 6.0;
+    v = 0.5 * (a0 + a1) - cs_limited_d2(d2, nb, 2) * (1.0 / 6.0);
   }
   return v;
 }

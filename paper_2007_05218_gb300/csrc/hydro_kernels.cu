@@ -374,18 +374,16 @@ constexpr double CS_C = 1.25;
 // CS08's branches (interface in bounds, zone or neighbour at an extremum,
 // second differences of one sign) are not continuous in their inputs: a
 // one-ulp change can move an edge value by the size of the limited
-// curvature.  So every quantity a branch depends on is formed with single
-// IEEE operations (no contraction into fused multiply-adds) in the order the
-// method writes them, and equal inputs give bitwise equal decisions and
-// edges on any IEEE machine.
+// curvature.  So every quantity a branch depends on (the interface values
+// included) is formed with single IEEE operations (no contraction into fused
+// multiply-adds) in the order the method writes them, and equal inputs give
+// bitwise equal decisions on any IEEE machine.
 __device__ __forceinline__ double ie_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ie_sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ie_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double ie_div(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float ie_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float ie_div(float a, float b) { return __fdiv_rn(a, b); }
 
 // second difference a - 2 b + c, as (a - 2 b) + c
 template <typename R>
@@ -415,7 +413,7 @@ __device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
   if (opp_sign(ie_sub(v, a0), ie_sub(a1, v))) {
     const R d2 = ie_mul(R(3), ie_add(ie_sub(a0, ie_mul(R(2), v)), a1));
     const R o[2] = {ie_d2(am, a0, a1), ie_d2(a0, a1, a2)};
-    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_div(cs_limited_d2<R, 2>(d2, o), R(6)));
+    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_mul(cs_limited_d2<R, 2>(d2, o), R(1.0 / 6.0)));
   }
   return v;
 }
@@ -437,31 +435,35 @@ __device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W
 // interface values L, Rt: CS08's limiter (§2.2) -- at an extremum of the zone
 // or of a neighbour the parabola keeps its shape with its curvature
 // 6 (L + Rt - 2 a0) limited by the neighbouring second differences, else the
-// CW84 overshoot rule -- then flattening by f.  Single IEEE operations, as
-// for cs_interface.
+// CW84 overshoot rule -- then flattening by f.  What a branch reads is formed
+// with single IEEE operations, as for cs_interface; the edge values the
+// branches then produce feed only continuous stages and take the fast path
+// (approximate reciprocal, fused multiply-adds).
 template <typename R>
 __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt) {
-  if (!same_sign(ie_sub(Rt, a0), ie_sub(a0, L)) || !same_sign(ie_sub(ap, a0), ie_sub(a0, am))) {
+  const R dL = ie_sub(L, a0), dR = ie_sub(Rt, a0);
+  if (!same_sign(dR, ie_sub(a0, L)) || !same_sign(ie_sub(ap, a0), ie_sub(a0, am))) {
     const R d2 = ie_mul(R(6), ie_sub(ie_add(L, Rt), ie_mul(R(2), a0)));
     const R o[3] = {ie_d2(amm, am, a0), ie_d2(am, a0, ap), ie_d2(a0, ap, app)};
     const R lim = cs_limited_d2<R, 3>(d2, o);
     if (is_pos(fabs(lim))) {
-      const R sc = ie_div(lim, d2);  // in (0, 1]
-      L = ie_add(a0, ie_mul(ie_sub(L, a0), sc));
-      Rt = ie_add(a0, ie_mul(ie_sub(Rt, a0), sc));
+      // lim / d2 in (0, 1]; a true divide when d2 is too small for the
+      // approximate reciprocal (subnormal range)
+      const R sc = fabs(d2) > R(1e-30) ? lim * nr_rcp(d2) : lim / d2;
+      L = a0 + dL * sc;
+      Rt = a0 + dR * sc;
     } else {
       L = a0;
       Rt = a0;
     }
-  } else if (!dgt(ie_mul(R(2), fabs(ie_sub(L, a0))), fabs(ie_sub(Rt, a0)))) {
-    Rt = ie_sub(a0, ie_mul(R(2), ie_sub(L, a0)));
-  } else if (!dgt(ie_mul(R(2), fabs(ie_sub(Rt, a0))), fabs(ie_sub(L, a0)))) {
-    L = ie_sub(a0, ie_mul(R(2), ie_sub(Rt, a0)));
+  } else if (!dgt(ie_mul(R(2), fabs(dL)), fabs(dR))) {
+    Rt = a0 - R(2) * dL;
+  } else if (!dgt(ie_mul(R(2), fabs(dR)), fabs(dL))) {
+    L = a0 - R(2) * dR;
   }
   if (is_pos(f)) {
-    const R g = ie_sub(R(1), f);
-    L = ie_add(ie_mul(f, a0), ie_mul(g, L));
-    Rt = ie_add(ie_mul(f, a0), ie_mul(g, Rt));
+    L = f * a0 + (R(1) - f) * L;
+    Rt = f * a0 + (R(1) - f) * Rt;
   }
 }
 
