@@ -105,7 +105,7 @@ enum TableId : int {
   TB_CTU2,
   NTABLES
 };
-constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 6, 3};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3};
 // tables of the precision-specific stage kernels exist once per compute type
 constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true};
 

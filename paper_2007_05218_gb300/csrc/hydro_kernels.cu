@@ -56,12 +56,16 @@ template <typename R>
 struct Consts;
 template <>
 struct Consts<double> {
+  // FP64 edge states keep their conserved form in HBM (FP64 arithmetic is the
+  // scarce resource); FP32 ones rebuild it where they are read (HBM traffic is)
+  static constexpr bool STORE_CONSERVED = true;
   static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
   static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
   static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
 };
 template <>
 struct Consts<float> {
+  static constexpr bool STORE_CONSERVED = false;
   static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
   static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
   static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
@@ -76,15 +80,27 @@ __device__ __forceinline__ long long zone(const DevBox& b, int i, int j, int k) 
   return (long long)(i + NG) + (long long)(j + NG) * b.s[1] + (long long)(k + NG) * b.s[2];
 }
 
-// linear thread index -> zone of the region lo[a] .. lo[a]+ext[a]-1 (x fastest)
+// linear thread index -> zone of the region lo[a] .. lo[a]+ext[a]-1 (x fastest).
+// Regions of fewer than 2^32 zones (every box up to about 1600^3) divide in
+// 32 bits -- a 64-bit integer division is a long software sequence, and this
+// runs once per thread of every stage; the test is uniform over a block.
 __device__ __forceinline__ bool decode(long long t, const int* lo, const int* ext, int* c) {
-  long long vol = (long long)ext[0] * ext[1] * ext[2];
-  if (t >= vol) return false;
-  long long r = t / ext[0];
-  c[0] = lo[0] + (int)(t - r * ext[0]);
-  long long k = r / ext[1];
-  c[1] = lo[1] + (int)(r - k * ext[1]);
-  c[2] = lo[2] + (int)k;
+  const unsigned long long vol = (unsigned long long)ext[0] * (unsigned)ext[1] * (unsigned)ext[2];
+  if ((unsigned long long)t >= vol) return false;
+  if (vol <= 0xffffffffull) {
+    const unsigned tt = (unsigned)t, e0 = (unsigned)ext[0], e1 = (unsigned)ext[1];
+    const unsigned r = tt / e0;
+    c[0] = lo[0] + (int)(tt - r * e0);
+    const unsigned k = r / e1;
+    c[1] = lo[1] + (int)(r - k * e1);
+    c[2] = lo[2] + (int)k;
+  } else {
+    const long long r = t / ext[0];
+    c[0] = lo[0] + (int)(t - r * ext[0]);
+    const long long k = r / ext[1];
+    c[1] = lo[1] + (int)(r - k * ext[1]);
+    c[2] = lo[2] + (int)k;
+  }
   return true;
 }
 
@@ -600,7 +616,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
-  store_conserved<R, D>(W, vs, Z, FLD_UP, out, igm1);
+  if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, FLD_UP, out, igm1);
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
   if (is_neg(lm)) {
@@ -636,7 +652,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
 #pragma unroll
   for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
-  store_conserved<R, D>(W, vs, Z, FLD_UM, out, igm1);
+  if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, FLD_UM, out, igm1);
 }
 
 template <typename R, int LIM>
@@ -815,19 +831,33 @@ __device__ __forceinline__ void riemann(const R* L, R El, const R* Rs, R Er, R g
 }
 
 // The two states of the D-face at zone Z: primitive q (5) and conserved
-// momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides.
+// momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides;
+// the conserved form is loaded (FP64) or rebuilt from q (FP32).
+template <typename R>
+__device__ __forceinline__ void conserved_of(const R* q, R igm1, R* u) {
+  u[0] = q[0] * q[1];
+  u[1] = q[0] * q[2];
+  u[2] = q[0] * q[3];
+  u[3] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+}
+
 template <typename R, int D>
 __device__ __forceinline__ void load_face_states(const R* __restrict__ W, long long vs, long long Z, long long sD,
-                                                 R* qL, R* uL, R* qR, R* uR) {
+                                                 R igm1, R* qL, R* uL, R* qR, R* uR) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     qL[m] = W[(FLD_QP + 5 * D + m) * vs + Z - sD];
     qR[m] = W[(FLD_QM + 5 * D + m) * vs + Z];
   }
+  if constexpr (Consts<R>::STORE_CONSERVED) {
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    uL[j] = W[(FLD_UP + 4 * D + j) * vs + Z - sD];
-    uR[j] = W[(FLD_UM + 4 * D + j) * vs + Z];
+    for (int j = 0; j < 4; j++) {
+      uL[j] = W[(FLD_UP + 4 * D + j) * vs + Z - sD];
+      uR[j] = W[(FLD_UM + 4 * D + j) * vs + Z];
+    }
+  } else {
+    conserved_of(qL, igm1, uL);
+    conserved_of(qR, igm1, uR);
   }
 }
 
@@ -840,7 +870,7 @@ __device__ __forceinline__ void store_flux(R* __restrict__ dst, long long vs, lo
 template <typename R, int D, int RS>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
-  load_face_states<R, D>(W, b.vs, Z, b.s[D], qL, uL, qR, uR);
+  load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
   riemann<R, RS>(qL, uL[3], qR, uR[3], Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
@@ -902,45 +932,78 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
 
-template <typename R, int D, int E, int RS>
-__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt) {
+// Stage 1 of the corner transport: the D-face at zone Z corrected by the
+// flux difference along one transverse axis T (the ordered pair (D, T)), for
+// each T in {E, F} the face carries: the face's two states are loaded once
+// for both pairs.
+template <typename R, int D, int T, int RS>
+__device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
+                                          const R* qL0, const R* uL, const R* qR0, const R* uR) {
   const long long vs = b.vs, sD = b.s[D];
   const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
-  R qL[5], qR[5], uL[4], uR[4], Fn[5];
-  load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
-  const R* Fb[1] = {W + (FLD_F0 + 5 * E) * vs};
-  const long long st[1] = {b.s[E]};
-  const R fac[1] = {Consts<R>::dtdx(b, rt, E) * R(1.0 / 3.0)};
+  R qL[5], qR[5], Fn[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    qL[m] = qL0[m];
+    qR[m] = qR0[m];
+  }
+  const R* Fb[1] = {W + (FLD_F0 + 5 * T) * vs};
+  const long long st[1] = {b.s[T]};
+  const R fac[1] = {Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0)};
   const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
   const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
   riemann<R, RS>(qL, EL, qR, ER, gamma, igm1, Fn);
-  store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, E)) * vs, vs, Z, Fn);
+  store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * vs, vs, Z, Fn);
 }
 
+// FP32: the two states stay in registers for both pairs.  FP64: each pair
+// loads them (the second load hits L1), so that 18 doubles are not held
+// across a Riemann solve -- registers, not HBM, limit the FP64 kernel.
+template <typename R, int D, int RS>
+__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
+                                          bool with_e, bool with_f) {
+  constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
+  R qL[5], qR[5], uL[4], uR[4];
+  if constexpr (Consts<R>::STORE_CONSERVED) {
+    if (with_e) {
+      load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
+      ctu1_pair<R, D, E, RS>(b, W, Z, rt, qL, uL, qR, uR);
+    }
+    if (with_f) {
+      load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
+      ctu1_pair<R, D, F, RS>(b, W, Z, rt, qL, uL, qR, uR);
+    }
+  } else {
+    load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
+    if (with_e) ctu1_pair<R, D, E, RS>(b, W, Z, rt, qL, uL, qR, uR);
+    if (with_f) ctu1_pair<R, D, F, RS>(b, W, Z, rt, qL, uL, qR, uR);
+  }
+}
+
+// One thread per D-face over faces [0, n_D] along D and [-1, n] across it:
+// pair (D, E) is defined where the E index is in [0, n_E - 1], pair (D, F)
+// where the F index is in [0, n_F - 1] (E = D+1, F = D+2 mod 3).
 template <typename R, int RS>
 __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __restrict__ boxes,
                                               const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   LOCATE(tv)
   if (!box_uses<R>(b)) return;
-  const int p = z_;  // pair slot: xy xz yx yz zx zy
-  const int d = p / 2, r = p % 2;
-  const int e = r == 0 ? (d == 0 ? 1 : 0) : (d == 2 ? 1 : 2);
-  const int f = 3 - d - e;
-  int lo[3], ext[3], c[3];
-  lo[d] = 0; ext[d] = b.n[d] + 1;
-  lo[e] = 0; ext[e] = b.n[e];
-  lo[f] = -1; ext[f] = b.n[f] + 2;
+  const int d = z_;
+  const int e = (d + 1) % 3, f = (d + 2) % 3;
+  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
+  lo[d] = 0;
+  ext[d] = b.n[d] + 1;
   if (!decode(t_, lo, ext, c)) return;
+  const bool with_e = c[e] >= 0 && c[e] < b.n[e];
+  const bool with_f = c[f] >= 0 && c[f] < b.n[f];
+  if (!with_e && !with_f) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   const BoxRt& rtb = rt[bi];
-  switch (p) {
-    case 0: ctu1_face<R, 0, 1, RS>(b, W, Z, rtb); break;
-    case 1: ctu1_face<R, 0, 2, RS>(b, W, Z, rtb); break;
-    case 2: ctu1_face<R, 1, 0, RS>(b, W, Z, rtb); break;
-    case 3: ctu1_face<R, 1, 2, RS>(b, W, Z, rtb); break;
-    case 4: ctu1_face<R, 2, 0, RS>(b, W, Z, rtb); break;
-    default: ctu1_face<R, 2, 1, RS>(b, W, Z, rtb); break;
+  switch (d) {
+    case 0: ctu1_face<R, 0, RS>(b, W, Z, rtb, with_e, with_f); break;
+    case 1: ctu1_face<R, 1, RS>(b, W, Z, rtb, with_e, with_f); break;
+    default: ctu1_face<R, 2, RS>(b, W, Z, rtb, with_e, with_f); break;
   }
 }
 
@@ -951,7 +1014,7 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   const long long vs = b.vs, sD = b.s[D];
   const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
-  load_face_states<R, D>(W, vs, Z, sD, qL, uL, qR, uR);
+  load_face_states<R, D>(W, vs, Z, sD, igm1, qL, uL, qR, uR);
   const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
   const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
@@ -1101,12 +1164,7 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
     case TB_TRACE: return (n[0] + 2) * (n[1] + 2) * (n[2] + 2);
     case TB_SLOPES: return (n[z] + 4) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_RIEMANN: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
-    case TB_CTU1: {
-      const int dd = z / 2, r = z % 2;
-      const int e = r == 0 ? (dd == 0 ? 1 : 0) : (dd == 2 ? 1 : 2);
-      const int f = 3 - dd - e;
-      return (n[dd] + 1) * n[e] * (n[f] + 2);
-    }
+    case TB_CTU1: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_CTU2: return (n[z] + 1) * n[(z + 1) % 3] * n[(z + 2) % 3];
     default: return 0;
   }
