@@ -59,6 +59,10 @@ struct Consts<double> {
   // FP64 edge states keep their conserved form in HBM (FP64 arithmetic is the
   // scarce resource); FP32 ones rebuild it where they are read (HBM traffic is)
   static constexpr bool STORE_CONSERVED = true;
+  // a corrected state's 1/rho comes from the 1/sqrt(rho) the Riemann solver
+  // needs (saves FP64 instructions; in FP32 the extra live register costs
+  // more occupancy than the reciprocal it saves)
+  static constexpr bool SHARE_RSQRT = true;
   static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
   static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
   static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
@@ -66,6 +70,7 @@ struct Consts<double> {
 template <>
 struct Consts<float> {
   static constexpr bool STORE_CONSERVED = false;
+  static constexpr bool SHARE_RSQRT = false;
   static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
   static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
   static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
@@ -683,11 +688,15 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // and three reciprocals; wave-speed min/max and sign tests run on the integer
 // pipe.
 template <typename R>
-__device__ __forceinline__ void hllc(const R* L, R El, const R* Rs, R Er, R gamma, R* F) {
+__device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R* F) {
   const R gm1 = gamma - R(1);
   const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
   const R rr = Rs[0], ur = Rs[1], vr = Rs[2], wr = Rs[3], pr = Rs[4];
-  const R rsl = nr_rsqrt(rl), rsr = nr_rsqrt(rr);  // 1/sqrt(rho)
+  // 1/sqrt(rho) of each side: from the caller where SHARE_RSQRT holds
+  if constexpr (!Consts<R>::SHARE_RSQRT) {
+    rsl = nr_rsqrt(rl);
+    rsr = nr_rsqrt(rr);
+  }
   const R sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
   const R irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
   const R gpl = gamma * pl, gpr = gamma * pr;
@@ -822,12 +831,13 @@ __device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R ig
   F[4] = (E + q4) * q1;
 }
 
-// The handle's Riemann solver.  El, Er: total energies of the states (HLLC
-// uses them; the two-shock flux is built from the sampled state alone).
+// The handle's Riemann solver.  El, Er: total energies of the states and rsl,
+// rsr their 1/sqrt(rho) (HLLC uses them; the two-shock flux is built from the
+// sampled state alone).
 template <typename R, int RS>
-__device__ __forceinline__ void riemann(const R* L, R El, const R* Rs, R Er, R gamma, R igm1, R* F) {
+__device__ __forceinline__ void riemann(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R igm1, R* F) {
   if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock(L, Rs, gamma, igm1, F);
-  else hllc(L, El, Rs, Er, gamma, F);
+  else hllc(L, El, rsl, Rs, Er, rsr, gamma, F);
 }
 
 // The two states of the D-face at zone Z: primitive q (5) and conserved
@@ -871,7 +881,10 @@ template <typename R, int D, int RS>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-  riemann<R, RS>(qL, uL[3], qR, uR[3], Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  const bool own = RS == HYDRO_RIEMANN_HLLC && Consts<R>::SHARE_RSQRT;
+  const R rsl = own ? nr_rsqrt(qL[0]) : R(0);
+  const R rsr = own ? nr_rsqrt(qR[0]) : R(0);
+  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
@@ -898,10 +911,13 @@ __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __r
 // Face state of zone Z (primitive q and conserved momenta + energy u, normal
 // frame of D) minus fac_t * (flux difference across zone Z along stride s_t)
 // for each term t, back to primitive.  A result with rho <= 0 or p <= 0 keeps
-// the uncorrected state.  Returns the total energy of the state that is kept.
+// the uncorrected state.  Returns the total energy of the state that is kept
+// and, in rs, 1/sqrt(rho) of it where SHARE_RSQRT holds: one reciprocal square
+// root gives both the 1/rho of the conversion (its square) and what the
+// Riemann solver needs (else rs is 0 and the solver forms its own).
 template <typename R, int D, int NT>
 __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
-                                     long long vs, long long Z, R gamma, R igm1) {
+                                     long long vs, long long Z, R gamma, R igm1, R& rs) {
   R U[5] = {q[0], u[0], u[1], u[2], u[3]};
 #pragma unroll
   for (int m = 0; m < 5; m++) {
@@ -910,15 +926,17 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
     for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * (Fb[t][off + st[t]] - Fb[t][off]);
   }
   if (is_pos(U[0])) {
-    const R ir = nr_rcp(U[0]);
+    const R r = Consts<R>::SHARE_RSQRT ? nr_rsqrt(U[0]) : R(0);
+    const R ir = Consts<R>::SHARE_RSQRT ? r * r : nr_rcp(U[0]);
     const R uu = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    const R kin = R(0.5) * U[0] * (uu * uu + v * v + w * w);
+    const R kin = R(0.5) * (U[1] * uu + U[2] * v + U[3] * w);
     const R p = (gamma - R(1)) * (U[4] - kin);
     if (is_pos(p)) {
       q[0] = U[0];
       q[1] = uu;
       q[2] = v;
       q[3] = w;
+      rs = r;
       if (dgt(R(SMALL_PRES), p)) {  // floored pressure: the energy follows it
         q[4] = R(SMALL_PRES);
         return q[4] * igm1 + kin;
@@ -927,6 +945,7 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
       return U[4];
     }
   }
+  rs = Consts<R>::SHARE_RSQRT ? nr_rsqrt(q[0]) : R(0);
   return u[3];
 }
 
@@ -950,9 +969,10 @@ __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, lo
   const R* Fb[1] = {W + (FLD_F0 + 5 * T) * vs};
   const long long st[1] = {b.s[T]};
   const R fac[1] = {Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0)};
-  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
-  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
-  riemann<R, RS>(qL, EL, qR, ER, gamma, igm1, Fn);
+  R rsl, rsr;
+  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1, rsl);
+  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1, rsr);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, igm1, Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * vs, vs, Z, Fn);
 }
 
@@ -1018,9 +1038,10 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
   const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
-  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1);
-  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1);
-  riemann<R, RS>(qL, EL, qR, ER, gamma, igm1, Fn);
+  R rsl, rsr;
+  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1, rsl);
+  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1, rsr);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, igm1, Fn);
   if (wall) {
     // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
     Fn[0] = R(0);
@@ -1098,9 +1119,10 @@ __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __re
   double nu[5];
   if (b.precision == HYDRO_FP64) update_zone(b, U, fields<double>(work, b), Z, dt, nu);
   else update_zone(b, U, fields<float>(work, b), Z, dt, nu);
-  const double kin = 0.5 * (nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3]) * nr_rcp(nu[0]);
-  const double p = (b.gamma - 1.0) * (nu[4] - kin);
-  if (!(nu[0] > 0.0) || !(p > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+  // rho > 0 and p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0, i.e. 2 rho E > |m|^2:
+  // no reciprocal; a NaN fails the tests
+  const double m2 = nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3];
+  if (!(nu[0] > 0.0) || !(2.0 * nu[0] * nu[4] - m2 > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
 }
 
 // ----------------------------------------------------- host staging transfers
