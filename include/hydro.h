@@ -230,6 +230,17 @@ typedef struct hydro_tuning {
 int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries, int* nentries, void* stream);
 int hydro_use_graphs(hydro_handle* h, int enable);
 
+/* Fused line stage.  For HYDRO_MIXED boxes under HYDRO_LIMITER_CW84 the slopes,
+ * the limited parabolas, the characteristic tracing and the normal Riemann
+ * solves of each axis run as one kernel per step (table "line" in
+ * hydro_autotune): they depend only on the zones of one line along the axis,
+ * so the line's values stay in registers and only the traced edge states and
+ * the normal fluxes reach HBM.  The arithmetic is that of the separate stages;
+ * the slope fields dq of hydro_debug_fields are then not written for those
+ * boxes, and the stage time of the fused kernel is reported under "trace".
+ * On by default; hydro_fuse_lines(h, 0) runs the separate stages. */
+int hydro_fuse_lines(hydro_handle* h, int enable);
+
 /* Number of kernels this handle has launched since hydro_alloc (a ghost fill
  * is three kernels, every other stage one per compute type present), into
  * *count. */

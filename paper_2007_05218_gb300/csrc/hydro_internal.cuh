@@ -103,11 +103,21 @@ enum TableId : int {
   TB_RIEMANN,
   TB_CTU1,
   TB_CTU2,
+  TB_LINE,  // fused slopes + tracing + normal Riemann solves along one axis (FP32 boxes)
   NTABLES
 };
-constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 3};
 // tables of the precision-specific stage kernels exist once per compute type
-constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true};
+constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true,
+                                               true};
+// the fused line stage runs for FP32 boxes only (slot 1): the FP64 stages are
+// bound by the FP64 pipe, which fusion does not relieve
+constexpr bool LINE_FUSED_SLOT[2] = {false, true};
+// zones a warp produces along x in the fused line stage (lanes 3..29 of 32;
+// the other lanes supply the stencil's neighbours by shuffle) and traced zones
+// a thread produces along y or z (walking a column)
+constexpr int LINE_X_OUT = 27;
+constexpr int LINE_SEG = 16;
 
 struct WorkTable {
   int* start;      // device, nitems + 1 entries (start[nitems] = blocks)
@@ -135,7 +145,13 @@ struct Plan {
   bool shared_dt = false;     // one dt for all boxes: the minimum of their CFL steps
   int limiter = HYDRO_LIMITER_CW84;   // reconstruction variant of every box
   int riemann = HYDRO_RIEMANN_HLLC;   // Riemann solver of every box
+  bool fuse_lines = true;             // fused line stage for FP32 boxes (CW84 limiter)
 };
+
+// Whether precision slot `slot` runs the fused line stage under this plan.
+inline bool line_fused(const Plan& p, int slot) {
+  return LINE_FUSED_SLOT[slot] && p.fuse_lines && p.limiter == HYDRO_LIMITER_CW84;
+}
 
 // Threads per block each table starts with (before any autotuning).
 int default_tpb(int table);

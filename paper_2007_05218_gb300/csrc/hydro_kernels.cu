@@ -550,32 +550,19 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
   W[(base + 4 * D + 3) * vs + Z] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
-template <typename R, int D, int LIM>
-__device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
-  const long long vs = b.vs, s = b.s[D];
-  const R igm1 = Consts<R>::igm1(b);
-  const R f = W[FLD_CHI * vs + Z];
-  R a0[5], aL[5], aR[5];
-#pragma unroll
-  for (int m = 0; m < 5; m++) {
-    const R* a = W + comp<D>(m) * vs + Z;
-    const R* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
-    a0[m] = a[0];
-    if constexpr (LIM == HYDRO_LIMITER_CS08) {
-      aL[m] = dq[0];
-      aR[m] = dq[s];
-      cs_parabola(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
-    } else {
-      parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
-    }
-  }
+// Characteristic tracing of one zone along one axis (Miller & Colella 2002
+// style, R4): zone values a0, limited parabola edges aL, aR of the five
+// normal-frame variables, zone sound speed cs, dt/dx.  Hands the right-edge
+// state (side 1, the left state of the zone's high face) and then the
+// left-edge state (side 0) to sink(side, q[5]) as soon as each is formed.
+template <typename R, typename Sink>
+__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R dtdx, Sink&& sink) {
   R dA[5], a6[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     dA[m] = aR[m] - aL[m];
     a6[m] = R(6) * (a0[m] - R(0.5) * (aL[m] + aR[m]));
   }
-  const R cs = W[FLD_C * vs + Z];
   const R rho = a0[0], u = a0[1];
   const R ic = nr_rcp(cs);
   const R rc = R(0.5) * rho * ic;   // rho / 2c
@@ -619,9 +606,7 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   }
   if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
-#pragma unroll
-  for (int m = 0; m < 5; m++) W[(FLD_QP + 5 * D + m) * vs + Z] = out[m];
-  if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, FLD_UP, out, igm1);
+  sink(1, out);
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
   if (is_neg(lm)) {
@@ -655,9 +640,34 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   }
   if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
   if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
+  sink(0, out);
+}
+
+template <typename R, int D, int LIM>
+__device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
+  const long long vs = b.vs, s = b.s[D];
+  const R igm1 = Consts<R>::igm1(b);
+  const R f = W[FLD_CHI * vs + Z];
+  R a0[5], aL[5], aR[5];
 #pragma unroll
-  for (int m = 0; m < 5; m++) W[(FLD_QM + 5 * D + m) * vs + Z] = out[m];
-  if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, FLD_UM, out, igm1);
+  for (int m = 0; m < 5; m++) {
+    const R* a = W + comp<D>(m) * vs + Z;
+    const R* dq = W + (FLD_DQ + 5 * D + m) * vs + Z;
+    a0[m] = a[0];
+    if constexpr (LIM == HYDRO_LIMITER_CS08) {
+      aL[m] = dq[0];
+      aR[m] = dq[s];
+      cs_parabola(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
+    } else {
+      parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
+    }
+  }
+  const R cs = W[FLD_C * vs + Z];
+  trace_edges(a0, aL, aR, cs, dtdx, [&](int side, const R* out) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) W[((side ? FLD_QP : FLD_QM) + 5 * D + m) * vs + Z] = out[m];
+    if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, side ? FLD_UP : FLD_UM, out, igm1);
+  });
 }
 
 template <typename R, int LIM>
@@ -1073,6 +1083,170 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
   }
 }
 
+// ---------------------------------------------------------- fused line stage
+// Slopes, parabolas, tracing and the normal Riemann solve of one axis depend
+// only on the zones of one line along that axis, so one kernel does all four
+// with the line's values in registers: it reads the primitive state, sound
+// speed and flattening coefficient once and writes only the traced edge states
+// and the normal fluxes (no slope fields, no second read of the edge states).
+// The arithmetic is the staged kernels' own (vl_slope, parabola, trace_edges,
+// the Riemann solver), CW84 limiter only.
+
+// Edge states of zone Z (normal frame of D) and, for FP64, their conserved form.
+template <typename R, int D>
+__device__ __forceinline__ void line_store_edges(R* __restrict__ W, long long vs, long long Z, const R* qm,
+                                                 const R* qp, R igm1) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    W[(FLD_QM + 5 * D + m) * vs + Z] = qm[m];
+    W[(FLD_QP + 5 * D + m) * vs + Z] = qp[m];
+  }
+  if constexpr (Consts<R>::STORE_CONSERVED) {
+    store_conserved<R, D>(W, vs, Z, FLD_UM, qm, igm1);
+    store_conserved<R, D>(W, vs, Z, FLD_UP, qp, igm1);
+  }
+}
+
+// Flux through the D-face between left state qL and right state qR, stored at
+// zone Z (the face's high-side zone).
+template <typename R, int D, int RS>
+__device__ __forceinline__ void line_normal_flux(const DevBox& b, R* __restrict__ W, long long Z, const R* qL,
+                                                 const R* qR) {
+  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  R uL[4], uR[4], Fn[5];
+  conserved_of(qL, igm1, uL);
+  conserved_of(qR, igm1, uR);
+  const bool own = RS == HYDRO_RIEMANN_HLLC && Consts<R>::SHARE_RSQRT;
+  const R rsl = own ? nr_rsqrt(qL[0]) : R(0);
+  const R rsr = own ? nr_rsqrt(qR[0]) : R(0);
+  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, gamma, igm1, Fn);
+  store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
+}
+
+// x lines: a warp holds 32 consecutive zones of one row, one per lane, and
+// gets each neighbour's value, slope and right-edge state by shuffle.  Lane l
+// of warp w in the row holds zone i = -1 + 27 w + l - 3; lanes 3..29 store
+// their zone's edge states (zones -1 .. n_x) and the flux through its low
+// face (faces 0 .. n_x), so consecutive warps tile the row.
+template <typename R, int RS>
+__device__ __forceinline__ void line_x(const DevBox& b, R* __restrict__ W, long long t, R dtdx) {
+  const int nx = b.n[0], ny2 = b.n[1] + 2;
+  const int wpr = (nx + 2 + LINE_X_OUT - 1) / LINE_X_OUT;
+  const long long per_row = (long long)wpr * 32;
+  if (t >= per_row * ny2 * (b.n[2] + 2)) return;  // whole warps only: per_row is a multiple of 32
+  const long long row = t / per_row;
+  const int rem = (int)(t - row * per_row);
+  const int lane = rem & 31;
+  const int i = -1 + LINE_X_OUT * (rem >> 5) + lane - 3;
+  const int j = (int)(row % ny2) - 1, k = (int)(row / ny2) - 1;
+  const long long vs = b.vs;
+  const long long Z = zone(b, min(i, nx + 3), j, k);  // lanes past the row's end load its last ghost
+  R a[5], dq[5], am[5], ap[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) a[m] = W[comp<0>(m) * vs + Z];
+  const R f = W[FLD_CHI * vs + Z], cs = W[FLD_C * vs + Z];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    am[m] = __shfl_up_sync(0xffffffffu, a[m], 1);
+    ap[m] = __shfl_down_sync(0xffffffffu, a[m], 1);
+    dq[m] = vl_slope(am[m], a[m], ap[m]);
+  }
+  R aL[5], aR[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    const R dm = __shfl_up_sync(0xffffffffu, dq[m], 1);
+    const R dp = __shfl_down_sync(0xffffffffu, dq[m], 1);
+    parabola(am[m], a[m], ap[m], dm, dq[m], dp, f, aL[m], aR[m]);
+  }
+  R qm[5], qp[5];
+  trace_edges(a, aL, aR, cs, dtdx, [&](int side, const R* out) {
+#pragma unroll
+    for (int m = 0; m < 5; m++) (side ? qp : qm)[m] = out[m];
+  });
+  R ql[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) ql[m] = __shfl_up_sync(0xffffffffu, qp[m], 1);
+  if (lane < 3 || lane > 29 || i > nx) return;
+  line_store_edges<R, 0>(W, vs, Z, qm, qp, Consts<R>::igm1(b));
+  if (i >= 0) line_normal_flux<R, 0, RS>(b, W, Z, ql, qm);
+}
+
+// y and z lines: a thread walks a segment of LINE_SEG zones of one column
+// along D (threads of a warp hold consecutive x, so every load and store is
+// coalesced), keeping the values of zones j-2..j+2 and the slopes of zones
+// j-1..j+1 in registers; the walk starts one zone early so that the first
+// face has its left state.
+template <typename R, int D, int RS>
+__device__ __forceinline__ void line_walk(const DevBox& b, R* __restrict__ W, long long t, R dtdx) {
+  constexpr int E = D == 1 ? 2 : 1;  // the transverse axis other than x
+  const int nx2 = b.n[0] + 2, ne2 = b.n[E] + 2, nd = b.n[D];
+  const int nseg = (nd + 2 + LINE_SEG - 1) / LINE_SEG;
+  if (t >= (long long)nx2 * ne2 * nseg) return;
+  const long long rest = t / nx2;
+  int c[3];
+  c[0] = (int)(t - rest * nx2) - 1;
+  c[E] = (int)(rest % ne2) - 1;
+  const int js = -1 + (int)(rest / ne2) * LINE_SEG;
+  const int je = min(js + LINE_SEG, nd + 1);  // traced zones [js, je), within [-1, n_D]
+  c[D] = js - 1;
+  const long long vs = b.vs, sD = b.s[D];
+  long long Z = zone(b, c[0], c[1], c[2]);
+  const R igm1 = Consts<R>::igm1(b);
+  R qv[5][5], dqv[3][5], qprev[5];
+#pragma unroll
+  for (int k = 0; k < 5; k++)
+#pragma unroll
+    for (int m = 0; m < 5; m++) qv[k][m] = W[comp<D>(m) * vs + Z + (k - 2) * sD];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int m = 0; m < 5; m++) dqv[k][m] = vl_slope(qv[k][m], qv[k + 1][m], qv[k + 2][m]);
+  for (int jz = js - 1; jz < je; jz++, Z += sD) {
+    const R f = W[FLD_CHI * vs + Z], cs = W[FLD_C * vs + Z];
+    R aL[5], aR[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) parabola(qv[1][m], qv[2][m], qv[3][m], dqv[0][m], dqv[1][m], dqv[2][m], f, aL[m], aR[m]);
+    R qm[5], qp[5];
+    trace_edges(qv[2], aL, aR, cs, dtdx, [&](int side, const R* out) {
+#pragma unroll
+      for (int m = 0; m < 5; m++) (side ? qp : qm)[m] = out[m];
+    });
+    if (jz >= js) {
+      line_store_edges<R, D>(W, vs, Z, qm, qp, igm1);
+      if (jz >= 0) line_normal_flux<R, D, RS>(b, W, Z, qprev, qm);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; m++) qprev[m] = qp[m];
+    if (jz + 1 < je) {  // slide the window one zone along D: zone jz+3 is at most n_D + 3
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qv[0][m] = qv[1][m];
+        qv[1][m] = qv[2][m];
+        qv[2][m] = qv[3][m];
+        qv[3][m] = qv[4][m];
+        qv[4][m] = W[comp<D>(m) * vs + Z + 3 * sD];
+        dqv[0][m] = dqv[1][m];
+        dqv[1][m] = dqv[2][m];
+        dqv[2][m] = vl_slope(qv[2][m], qv[3][m], qv[4][m]);
+      }
+    }
+  }
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_line(TableView tv, const DevBox* __restrict__ boxes,
+                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
+  if (!box_uses<R>(b)) return;
+  R* W = fields<R>(work, b);
+  const BoxRt& r = rt[bi];
+  switch (z_) {
+    case 0: line_x<R, RS>(b, W, t_, Consts<R>::dtdx(b, r, 0)); break;
+    case 1: line_walk<R, 1, RS>(b, W, t_, Consts<R>::dtdx(b, r, 1)); break;
+    default: line_walk<R, 2, RS>(b, W, t_, Consts<R>::dtdx(b, r, 2)); break;
+  }
+}
+
 // --------------------------------------------------------------------- update
 // FP32 -> FP64 on the integer pipe (the conversion instruction would occupy
 // the FP64 pipe): exact for normal floats; zero, subnormal floats (below
@@ -1156,11 +1330,12 @@ const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten"
                                            "riemann", "ctu1", "ctu2", "update"};
 
 const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
-                                           "slopes", "trace", "riemann", "ctu1", "ctu2"};
+                                           "slopes", "trace", "riemann", "ctu1", "ctu2", "line"};
 
 int default_tpb(int table) {
   switch (table) {
     case TB_TRACE:
+    case TB_LINE:
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
@@ -1188,6 +1363,9 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
     case TB_RIEMANN: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_CTU1: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_CTU2: return (n[z] + 1) * n[(z + 1) % 3] * n[(z + 2) % 3];
+    case TB_LINE:
+      if (z == 0) return (n[1] + 2) * (n[2] + 2) * ((n[0] + 2 + LINE_X_OUT - 1) / LINE_X_OUT) * 32;
+      return (n[0] + 2) * (n[z == 1 ? 2 : 1] + 2) * ((n[z] + 2 + LINE_SEG - 1) / LINE_SEG);
     default: return 0;
   }
 }
@@ -1255,13 +1433,28 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
     case TB_CTU2:
       return ts ? launch(k_ctu2<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
                 : launch(k_ctu2<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    case TB_LINE:
+      return ts ? launch(k_line<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                : launch(k_line<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
     default: return 0;
   }
 }
 
+// Stage table of one compute type, with the fused line stage standing in for
+// slopes (nothing), tracing (the line kernel) and the normal Riemann solves
+// (nothing) where it applies.
+template <typename R>
+int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
+  if (line_fused(p, slot)) {
+    if (table == TB_SLOPES || table == TB_RIEMANN) return 0;
+    if (table == TB_TRACE) return launch_typed<R>(p, TB_LINE, p.tab[TB_LINE][slot], s);
+  }
+  return launch_typed<R>(p, table, p.tab[table][slot], s);
+}
+
 // Both compute types of a per-precision table.
 int launch_both(const Plan& p, int table, cudaStream_t s) {
-  return launch_typed<double>(p, table, p.tab[table][0], s) + launch_typed<float>(p, table, p.tab[table][1], s);
+  return launch_slot<double>(p, table, 0, s) + launch_slot<float>(p, table, 1, s);
 }
 
 }  // namespace
@@ -1321,6 +1514,7 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
+    case TB_LINE:
       if (slot == 0) launch_typed<double>(p, table, w, stream);
       else launch_typed<float>(p, table, w, stream);
       break;

@@ -37,7 +37,7 @@ EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_fr
             "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
             "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
             "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_set_method",
-            "hydro_last_error")
+            "hydro_fuse_lines", "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -123,6 +123,7 @@ def load(path: str | None = None):
         L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
         L.hydro_autotune.argtypes = [_VP, i, ctypes.POINTER(hydro_tuning), i, ctypes.POINTER(i), _VP]
         L.hydro_use_graphs.argtypes = [_VP, i]
+        L.hydro_fuse_lines.argtypes = [_VP, i]
         L.hydro_set_neighbors.argtypes = [_VP, _VP]
         L.hydro_set_shared_dt.argtypes = [_VP, i]
         L.hydro_set_method.argtypes = [_VP, i, i]
@@ -297,6 +298,10 @@ def hydro_set_method(h: int, limiter: int = 0, riemann: int = 0) -> None:
 
 def hydro_use_graphs(h: int, enable: bool) -> None:
     _check(load().hydro_use_graphs(h, int(bool(enable))))
+
+
+def hydro_fuse_lines(h: int, enable: bool) -> None:
+    _check(load().hydro_fuse_lines(h, int(bool(enable))))
 
 
 def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:

@@ -123,3 +123,50 @@ def test_mixed_full_size_shear_layer_512_against_fp64_path():
     U0 = pr.U.reshape(5, -1)
     for v in (0, 4):  # reflecting y walls conserve mass and energy
         assert abs(sums[v] - U0[v].sum()) <= 1e-13 * np.sqrt(nsteps) * np.abs(U0[v]).sum() * 3
+
+
+def _one_step_fields(pr, fuse, riemann=0):
+    import torch
+    box = oracle.box_of(pr)
+    Ug = oracle.embed(pr.U)
+    oracle.fill_ghosts(box, Ug)
+    dt = oracle.compute_dt(box, Ug)
+    B = hydro.Boxes([pr], precision=hydro.HYDRO_MIXED, riemann=riemann)
+    hydro.hydro_fuse_lines(B.h, fuse)
+    B.step(1, dt=torch.tensor([dt], dtype=torch.float64, device="cuda"))
+    B.sync()
+    W = B.field_view(0, 0, oracle.W_NFIELDS).cpu().numpy().astype(np.float64)
+    U = B.interior(0)
+    B.close()
+    return W, U
+
+
+@pytest.mark.parametrize("riemann", [hydro.HYDRO_RIEMANN_HLLC, hydro.HYDRO_RIEMANN_TWO_SHOCK])
+@pytest.mark.parametrize("make", [lambda: inputs.sedov((31, 29, 17), seed=6),
+                                  lambda: inputs.density_wave((4, 5, 6), seed=2),
+                                  lambda: inputs.kelvin_helmholtz((60, 4, 33), seed=3)])
+def test_fused_line_stage_matches_the_separate_stages(make, riemann):
+    """The fused line kernel (slopes + parabolas + tracing + normal Riemann
+    solves per axis, FP32) computes what the separate FP32 stages compute:
+    the edge states, normal fluxes and updated state of one step agree to
+    FP32 rounding (the two builds may fuse multiply-adds differently) on
+    rows that do not fill whole warps and columns that do not fill whole
+    segments."""
+    pr = make()
+    Wf, Uf = _one_step_fields(pr, True, riemann)
+    Ws, Us = _one_step_fields(pr, False, riemann)
+    G = hydro.HYDRO_NG
+    ext = tuple(slice(G - 1, G + n + 1) for n in pr.shape[::-1])
+    for base in (oracle.W_QM, oracle.W_QP, oracle.W_F0):
+        for g in range(3):
+            blk = slice(base + 5 * g, base + 5 * g + 5)
+            a, b = Wf[blk][(slice(None),) + ext], Ws[blk][(slice(None),) + ext]
+            if base == oracle.W_F0:   # fluxes are defined on faces 0..n along their axis
+                sl = [slice(None)] * 4
+                sl[3 - g] = slice(1, pr.shape[g] + 2)
+                a, b = a[tuple(sl)], b[tuple(sl)]
+            scale = np.max(np.abs(b)) + 1e-30
+            assert np.all(np.isfinite(a)), (base, g)
+            assert np.max(np.abs(a - b)) <= 1e-6 * scale, (base, g)
+    for v in range(5):
+        assert np.max(np.abs(Uf[v] - Us[v])) <= 1e-6 * (np.max(np.abs(Us[v])) + 1e-30), v
