@@ -91,4 +91,22 @@ __device__ __forceinline__ R dmax(R a, R b) { return dkey(a) >= dkey(b) ? a : b;
 template <typename R>
 __device__ __forceinline__ bool dgt(R a, R b) { return dkey(a) > dkey(b); }
 
+// FP32 keeps its comparisons and min/max native: the FP32 units are not the
+// scarce resource there, and one native instruction replaces the several
+// integer ones of the bit-pattern forms (same results for finite inputs).
+template <>
+__device__ __forceinline__ float dmin<float>(float a, float b) { return fminf(a, b); }
+template <>
+__device__ __forceinline__ float dmax<float>(float a, float b) { return fmaxf(a, b); }
+template <>
+__device__ __forceinline__ bool dgt<float>(float a, float b) { return a > b; }
+template <>
+__device__ __forceinline__ bool is_pos<float>(float x) { return x > 0.0f; }
+template <>
+__device__ __forceinline__ bool is_neg<float>(float x) { return x < 0.0f; }
+template <>
+__device__ __forceinline__ bool same_sign<float>(float x, float y) { return x * y > 0.0f; }
+template <>
+__device__ __forceinline__ bool opp_sign<float>(float x, float y) { return x * y < 0.0f; }
+
 }  // namespace hydro

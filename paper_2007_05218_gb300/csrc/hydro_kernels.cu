@@ -353,6 +353,14 @@ __device__ __forceinline__ R vl_slope(R am, R a0, R ap) {
   return copysign(from_bits(m), dc);
 }
 
+template <>
+__device__ __forceinline__ float vl_slope<float>(float am, float a0, float ap) {
+  const float dl = a0 - am, dr = ap - a0;
+  if (!same_sign(dl, dr)) return 0.0f;
+  const float dc = 0.5f * (ap - am);
+  return copysignf(fminf(fabsf(dc), fminf(2.0f * fabsf(dl), 2.0f * fabsf(dr))), dc);
+}
+
 // FP64 form: the halving and doublings are exponent shifts of the bit
 // patterns, so the FP64 pipe only sees the three subtractions.  A shift is
 // exact only while the number and its result stay normal; differences near
