@@ -232,8 +232,9 @@ int hydro_use_graphs(hydro_handle* h, int enable);
 
 /* Fused line stage.  For HYDRO_MIXED boxes under HYDRO_LIMITER_CW84 the slopes,
  * the limited parabolas, the characteristic tracing and the normal Riemann
- * solves of each axis run as one kernel per step (table "line" in
- * hydro_autotune): they depend only on the zones of one line along the axis,
+ * solves of each axis run fused, one kernel for the x lines and one for the y
+ * and z lines (tables "line_x" and "line_yz" in hydro_autotune): they depend
+ * only on the zones of one line along the axis,
  * so the line's values stay in registers and only the traced edge states and
  * the normal fluxes reach HBM.  The arithmetic is that of the separate stages;
  * the slope fields dq of hydro_debug_fields are then not written for those

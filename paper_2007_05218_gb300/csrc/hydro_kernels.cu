@@ -527,10 +527,17 @@ __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __re
 // Parabola of zone value a0 with neighbours am1, ap1 and limited slopes
 // dm1, d0, dp1: interface values (CW84 eq. 1.6), monotonicity limiter
 // (eq. 1.10) with its tests on the integer pipe, then flattening by f.
+// 4th-order value at the face between zones of values am1, a0 and limited
+// slopes dm1, d0 (CW84 eq. 1.6).
 template <typename R>
-__device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1, R f, R& L, R& Rt) {
-  L = am1 + R(0.5) * (a0 - am1) - (d0 - dm1) * R(1.0 / 6.0);
-  Rt = a0 + R(0.5) * (ap1 - a0) - (dp1 - d0) * R(1.0 / 6.0);
+__device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
+  return am1 + R(0.5) * (a0 - am1) - (d0 - dm1) * R(1.0 / 6.0);
+}
+
+// CW84 monotonicity limiter of the parabola of zone value a0 between face
+// values L, Rt, then the flattening blend with coefficient f.
+template <typename R>
+__device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   if (!same_sign(Rt - a0, a0 - L)) {
     L = a0;
     Rt = a0;
@@ -545,6 +552,13 @@ __device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1,
     L = f * a0 + (R(1) - f) * L;
     Rt = f * a0 + (R(1) - f) * Rt;
   }
+}
+
+template <typename R>
+__device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1, R f, R& L, R& Rt) {
+  L = ppm_face(am1, a0, dm1, d0);
+  Rt = ppm_face(a0, ap1, d0, dp1);
+  cw84_limit(a0, f, L, Rt);
 }
 
 // Conserved momenta (normal frame) and total energy of a traced edge state,
@@ -1162,9 +1176,10 @@ __device__ __forceinline__ void line_x(const DevBox& b, R* __restrict__ W, long 
   R aL[5], aR[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
-    const R dm = __shfl_up_sync(0xffffffffu, dq[m], 1);
-    const R dp = __shfl_down_sync(0xffffffffu, dq[m], 1);
-    parabola(am[m], a[m], ap[m], dm, dq[m], dp, f, aL[m], aR[m]);
+    // this lane's low face; the high face is the next lane's low face
+    aL[m] = ppm_face(am[m], a[m], __shfl_up_sync(0xffffffffu, dq[m], 1), dq[m]);
+    aR[m] = __shfl_down_sync(0xffffffffu, aL[m], 1);
+    cw84_limit(a[m], f, aL[m], aR[m]);
   }
   R qm[5], qp[5];
   trace_edges(a, aL, aR, cs, dtdx, [&](int side, const R* out) {
@@ -1181,9 +1196,10 @@ __device__ __forceinline__ void line_x(const DevBox& b, R* __restrict__ W, long 
 
 // y and z lines: a thread walks a segment of LINE_SEG zones of one column
 // along D (threads of a warp hold consecutive x, so every load and store is
-// coalesced), keeping the values of zones j-2..j+2 and the slopes of zones
-// j-1..j+1 in registers; the walk starts one zone early so that the first
-// face has its left state.
+// coalesced).  Between zones it keeps only the values of zones j and j+1, the
+// slope of zone j, the value at the zone's low face (the previous zone's high
+// face) and the previous zone's right-edge state; the walk starts one zone
+// early so that the first face has its left state.
 template <typename R, int D, int RS>
 __device__ __forceinline__ void line_walk(const DevBox& b, R* __restrict__ W, long long t, R dtdx) {
   constexpr int E = D == 1 ? 2 : 1;  // the transverse axis other than x
@@ -1198,24 +1214,38 @@ __device__ __forceinline__ void line_walk(const DevBox& b, R* __restrict__ W, lo
   const int je = min(js + LINE_SEG, nd + 1);  // traced zones [js, je), within [-1, n_D]
   c[D] = js - 1;
   const long long vs = b.vs, sD = b.s[D];
-  long long Z = zone(b, c[0], c[1], c[2]);
+  long long Z = zone(b, c[0], c[1], c[2]);  // zone js - 1, the first one traced
   const R igm1 = Consts<R>::igm1(b);
-  R qv[5][5], dqv[3][5], qprev[5];
+  R q0[5], q1[5], q2[5], d0[5], fl[5], qprev[5];
 #pragma unroll
-  for (int k = 0; k < 5; k++)
-#pragma unroll
-    for (int m = 0; m < 5; m++) qv[k][m] = W[comp<D>(m) * vs + Z + (k - 2) * sD];
-#pragma unroll
-  for (int k = 0; k < 3; k++)
-#pragma unroll
-    for (int m = 0; m < 5; m++) dqv[k][m] = vl_slope(qv[k][m], qv[k + 1][m], qv[k + 2][m]);
+  for (int m = 0; m < 5; m++) {
+    const R* a = W + comp<D>(m) * vs + Z;
+    const R qa = a[-2 * sD], qb = a[-sD];  // zones js-3, js-2 (at least the last ghost)
+    q0[m] = a[0];
+    q1[m] = a[sD];
+    q2[m] = a[2 * sD];
+    const R db = vl_slope(qa, qb, q0[m]);
+    d0[m] = vl_slope(qb, q0[m], q1[m]);
+    fl[m] = ppm_face(qb, q0[m], db, d0[m]);
+  }
+#pragma unroll 1
   for (int jz = js - 1; jz < je; jz++, Z += sD) {
     const R f = W[FLD_CHI * vs + Z], cs = W[FLD_C * vs + Z];
-    R aL[5], aR[5];
+    R a0[5], aL[5], aR[5];
 #pragma unroll
-    for (int m = 0; m < 5; m++) parabola(qv[1][m], qv[2][m], qv[3][m], dqv[0][m], dqv[1][m], dqv[2][m], f, aL[m], aR[m]);
+    for (int m = 0; m < 5; m++) {
+      const R d1 = vl_slope(q0[m], q1[m], q2[m]);  // slope of zone jz+1
+      a0[m] = q0[m];
+      aL[m] = fl[m];
+      aR[m] = ppm_face(q0[m], q1[m], d0[m], d1);
+      fl[m] = aR[m];  // the next zone's low face, before this zone's limiter
+      cw84_limit(a0[m], f, aL[m], aR[m]);
+      d0[m] = d1;
+      q0[m] = q1[m];
+      q1[m] = q2[m];
+    }
     R qm[5], qp[5];
-    trace_edges(qv[2], aL, aR, cs, dtdx, [&](int side, const R* out) {
+    trace_edges(a0, aL, aR, cs, dtdx, [&](int side, const R* out) {
 #pragma unroll
       for (int m = 0; m < 5; m++) (side ? qp : qm)[m] = out[m];
     });
@@ -1225,34 +1255,31 @@ __device__ __forceinline__ void line_walk(const DevBox& b, R* __restrict__ W, lo
     }
 #pragma unroll
     for (int m = 0; m < 5; m++) qprev[m] = qp[m];
-    if (jz + 1 < je) {  // slide the window one zone along D: zone jz+3 is at most n_D + 3
+    if (jz + 1 < je) {  // zone jz+3: at most n_D + 2
 #pragma unroll
-      for (int m = 0; m < 5; m++) {
-        qv[0][m] = qv[1][m];
-        qv[1][m] = qv[2][m];
-        qv[2][m] = qv[3][m];
-        qv[3][m] = qv[4][m];
-        qv[4][m] = W[comp<D>(m) * vs + Z + 3 * sD];
-        dqv[0][m] = dqv[1][m];
-        dqv[1][m] = dqv[2][m];
-        dqv[2][m] = vl_slope(qv[2][m], qv[3][m], qv[4][m]);
-      }
+      for (int m = 0; m < 5; m++) q2[m] = W[comp<D>(m) * vs + Z + 3 * sD];
     }
   }
 }
 
+// Two kernels: the x lines need a third of the registers of the column walks
+// (no stencil window), so they run at twice the occupancy on their own.
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_line(TableView tv, const DevBox* __restrict__ boxes,
-                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+__global__ void __launch_bounds__(256) k_line_x(TableView tv, const DevBox* __restrict__ boxes,
+                                                const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
+  if (!box_uses<R>(b)) return;
+  line_x<R, RS>(b, fields<R>(work, b), t_, Consts<R>::dtdx(b, rt[bi], 0));
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_line_yz(TableView tv, const DevBox* __restrict__ boxes,
+                                                 const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   LOCATE(tv)
   if (!box_uses<R>(b)) return;
   R* W = fields<R>(work, b);
-  const BoxRt& r = rt[bi];
-  switch (z_) {
-    case 0: line_x<R, RS>(b, W, t_, Consts<R>::dtdx(b, r, 0)); break;
-    case 1: line_walk<R, 1, RS>(b, W, t_, Consts<R>::dtdx(b, r, 1)); break;
-    default: line_walk<R, 2, RS>(b, W, t_, Consts<R>::dtdx(b, r, 2)); break;
-  }
+  if (z_ == 0) line_walk<R, 1, RS>(b, W, t_, Consts<R>::dtdx(b, rt[bi], 1));
+  else line_walk<R, 2, RS>(b, W, t_, Consts<R>::dtdx(b, rt[bi], 2));
 }
 
 // --------------------------------------------------------------------- update
@@ -1338,12 +1365,13 @@ const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten"
                                            "riemann", "ctu1", "ctu2", "update"};
 
 const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
-                                           "slopes", "trace", "riemann", "ctu1", "ctu2", "line"};
+                                           "slopes", "trace", "riemann", "ctu1", "ctu2", "line_x", "line_yz"};
 
 int default_tpb(int table) {
   switch (table) {
     case TB_TRACE:
-    case TB_LINE:
+    case TB_LINE_X:
+    case TB_LINE_YZ:
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
@@ -1371,9 +1399,11 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
     case TB_RIEMANN: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_CTU1: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_CTU2: return (n[z] + 1) * n[(z + 1) % 3] * n[(z + 2) % 3];
-    case TB_LINE:
-      if (z == 0) return (n[1] + 2) * (n[2] + 2) * ((n[0] + 2 + LINE_X_OUT - 1) / LINE_X_OUT) * 32;
-      return (n[0] + 2) * (n[z == 1 ? 2 : 1] + 2) * ((n[z] + 2 + LINE_SEG - 1) / LINE_SEG);
+    case TB_LINE_X: return (n[1] + 2) * (n[2] + 2) * ((n[0] + 2 + LINE_X_OUT - 1) / LINE_X_OUT) * 32;
+    case TB_LINE_YZ: {
+      const int dd = z + 1;  // walk axis: y, then z
+      return (n[0] + 2) * (n[dd == 1 ? 2 : 1] + 2) * ((n[dd] + 2 + LINE_SEG - 1) / LINE_SEG);
+    }
     default: return 0;
   }
 }
@@ -1441,9 +1471,12 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
     case TB_CTU2:
       return ts ? launch(k_ctu2<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
                 : launch(k_ctu2<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
-    case TB_LINE:
-      return ts ? launch(k_line<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
-                : launch(k_line<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    case TB_LINE_X:
+      return ts ? launch(k_line_x<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                : launch(k_line_x<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    case TB_LINE_YZ:
+      return ts ? launch(k_line_yz<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                : launch(k_line_yz<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
     default: return 0;
   }
 }
@@ -1455,7 +1488,9 @@ template <typename R>
 int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
   if (line_fused(p, slot)) {
     if (table == TB_SLOPES || table == TB_RIEMANN) return 0;
-    if (table == TB_TRACE) return launch_typed<R>(p, TB_LINE, p.tab[TB_LINE][slot], s);
+    if (table == TB_TRACE)
+      return launch_typed<R>(p, TB_LINE_X, p.tab[TB_LINE_X][slot], s) +
+             launch_typed<R>(p, TB_LINE_YZ, p.tab[TB_LINE_YZ][slot], s);
   }
   return launch_typed<R>(p, table, p.tab[table][slot], s);
 }
@@ -1522,7 +1557,8 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
-    case TB_LINE:
+    case TB_LINE_X:
+    case TB_LINE_YZ:
       if (slot == 0) launch_typed<double>(p, table, w, stream);
       else launch_typed<float>(p, table, w, stream);
       break;
