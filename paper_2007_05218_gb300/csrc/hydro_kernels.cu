@@ -947,15 +947,28 @@ __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __r
 // and, in rs, 1/sqrt(rho) of it where SHARE_RSQRT holds: one reciprocal square
 // root gives both the 1/rho of the conversion (its square) and what the
 // Riemann solver needs (else rs is 0 and the solver forms its own).
+// Flux differences across zone Z along stride st[t] of the fluxes Fb[t], per
+// normal-frame variable m: dlt[t][m].
 template <typename R, int D, int NT>
-__device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
-                                     long long vs, long long Z, R gamma, R igm1, R& rs) {
-  R U[5] = {q[0], u[0], u[1], u[2], u[3]};
+__device__ __forceinline__ void flux_deltas(const R* const* Fb, const long long* st, long long vs, long long Z,
+                                            R (*dlt)[5]) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const long long off = comp<D>(m) * vs + Z;
 #pragma unroll
-    for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * (Fb[t][off + st[t]] - Fb[t][off]);
+    for (int t = 0; t < NT; t++) dlt[t][m] = Fb[t][off + st[t]] - Fb[t][off];
+  }
+}
+
+// The correction itself, from the flux differences (see correct).
+template <typename R, int NT>
+__device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], const R* fac, R gamma, R igm1,
+                                        R& rs) {
+  R U[5] = {q[0], u[0], u[1], u[2], u[3]};
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+#pragma unroll
+    for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * dlt[t][m];
   }
   if (is_pos(U[0])) {
     const R r = Consts<R>::SHARE_RSQRT ? nr_rsqrt(U[0]) : R(0);
@@ -979,6 +992,14 @@ __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const
   }
   rs = Consts<R>::SHARE_RSQRT ? nr_rsqrt(q[0]) : R(0);
   return u[3];
+}
+
+template <typename R, int D, int NT>
+__device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
+                                     long long vs, long long Z, R gamma, R igm1, R& rs) {
+  R dlt[NT][5];
+  flux_deltas<R, D, NT>(Fb, st, vs, Z, dlt);
+  return correct_by<R, NT>(q, u, dlt, fac, gamma, igm1, rs);
 }
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
@@ -1282,6 +1303,143 @@ __global__ void __launch_bounds__(256) k_line_yz(TableView tv, const DevBox* __r
   else line_walk<R, 2, RS>(b, W, t_, Consts<R>::dtdx(b, rt[bi], 2));
 }
 
+// ------------------------------------------------ CTU stage 2 along lines
+// The final correction of a zone's two D-edge states uses the same flux
+// differences across the zone (of the once-corrected fluxes along the two
+// transverse axes), so a thread that owns zones rather than faces loads them
+// once for both edges and hands the corrected right-edge state on to the next
+// face (FP32 boxes; same arithmetic as k_ctu2).
+
+// Zone Z's two D-edge states (raw) and the flux differences across the zone
+// that stage 2 corrects them with.
+template <typename R, int D>
+struct Ctu2Zone {
+  R qm[5], qp[5], dlt[2][5];
+};
+
+template <typename R, int D>
+__device__ __forceinline__ void ctu2_load(const DevBox& b, const R* __restrict__ W, long long Z, Ctu2Zone<R, D>& z) {
+  constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
+  const long long vs = b.vs;
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    z.qm[m] = W[(FLD_QM + 5 * D + m) * vs + Z];
+    z.qp[m] = W[(FLD_QP + 5 * D + m) * vs + Z];
+  }
+  const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
+  const long long st[2] = {b.s[E], b.s[F]};
+  flux_deltas<R, D, 2>(Fb, st, vs, Z, z.dlt);
+}
+
+// Both edge states of a loaded zone corrected by stage 2 (in place), with
+// their energies and 1/sqrt(rho).  FP32 boxes only (conserved form rebuilt).
+template <typename R, int D>
+__device__ __forceinline__ void ctu2_correct(const DevBox& b, Ctu2Zone<R, D>& z, const R* fac, R& Em, R& rsm,
+                                             R& Ep, R& rsp) {
+  static_assert(!Consts<R>::STORE_CONSERVED, "zone-wise stage 2 runs for FP32 boxes");
+  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  R um[4], up[4];
+  conserved_of(z.qm, igm1, um);
+  conserved_of(z.qp, igm1, up);
+  Em = correct_by<R, 2>(z.qm, um, z.dlt, fac, gamma, igm1, rsm);
+  Ep = correct_by<R, 2>(z.qp, up, z.dlt, fac, gamma, igm1, rsp);
+}
+
+// Final flux through the low D-face of zone Z from the corrected states.
+template <typename R, int D, int RS>
+__device__ __forceinline__ void ctu2_flux(const DevBox& b, R* __restrict__ W, long long Z, int face, R* qL, R EL,
+                                          R rsl, R* qR, R ER, R rsr) {
+  R Fn[5];
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  const bool wall = (face == 0 && b.bc[2 * D] == HYDRO_BC_REFLECT && b.nbr1[2 * D] == 0) ||
+                    (face == b.n[D] && b.bc[2 * D + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * D + 1] == 0);
+  if (wall) {  // impermeable: only the normal momentum flux (the wall pressure) remains
+    Fn[0] = R(0);
+    Fn[2] = R(0);
+    Fn[3] = R(0);
+    Fn[4] = R(0);
+  }
+  store_flux<R, D>(W + (FLD_F + 5 * D) * b.vs, b.vs, Z, Fn);
+}
+
+// x faces: lane l of warp w in an interior row owns zone i = -1 + 31 w + l and,
+// for l >= 1, the face at its low side (faces 0 .. n_x); the left state comes
+// from lane l-1 by shuffle.
+template <typename R, int RS>
+__device__ __forceinline__ void ctu2_x(const DevBox& b, R* __restrict__ W, long long t, const BoxRt& rt) {
+  const int nx = b.n[0], ny = b.n[1];
+  const int wpr = (nx + 1 + 30) / 31;
+  const long long per_row = (long long)wpr * 32;
+  if (t >= per_row * ny * b.n[2]) return;  // whole warps only
+  const long long row = t / per_row;
+  const int rem = (int)(t - row * per_row);
+  const int lane = rem & 31;
+  const int i = -1 + 31 * (rem >> 5) + lane;
+  const long long Z = zone(b, min(i, nx), (int)(row % ny), (int)(row / ny));
+  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, 1), R(0.5) * Consts<R>::dtdx(b, rt, 2)};
+  Ctu2Zone<R, 0> z;
+  R Em, Ep, rsm, rsp;
+  ctu2_load<R, 0>(b, W, Z, z);
+  ctu2_correct<R, 0>(b, z, fac, Em, rsm, Ep, rsp);
+  R ql[5];
+#pragma unroll
+  for (int m = 0; m < 5; m++) ql[m] = __shfl_up_sync(0xffffffffu, z.qp[m], 1);
+  const R El = __shfl_up_sync(0xffffffffu, Ep, 1), rsl = __shfl_up_sync(0xffffffffu, rsp, 1);
+  if (lane == 0 || i > nx) return;
+  ctu2_flux<R, 0, RS>(b, W, Z, i, ql, El, rsl, z.qm, Em, rsm);
+}
+
+// y and z faces: a thread walks LINE_SEG faces of one interior column.
+template <typename R, int D, int RS>
+__device__ __forceinline__ void ctu2_walk(const DevBox& b, R* __restrict__ W, long long t, const BoxRt& rt) {
+  constexpr int O = D == 1 ? 2 : 1;  // the transverse axis other than x
+  constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
+  const int nx = b.n[0], no = b.n[O], nd = b.n[D];
+  const int nseg = (nd + 1 + LINE_SEG - 1) / LINE_SEG;
+  if (t >= (long long)nx * no * nseg) return;
+  const long long rest = t / nx;
+  int c[3];
+  c[0] = (int)(t - rest * nx);
+  c[O] = (int)(rest % no);
+  const int fs = (int)(rest / no) * LINE_SEG;
+  const int fe = min(fs + LINE_SEG, nd + 1);  // faces [fs, fe), within [0, n_D]
+  c[D] = fs - 1;
+  const long long sD = b.s[D];
+  long long Z = zone(b, c[0], c[1], c[2]);
+  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
+  Ctu2Zone<R, D> z;
+  R ql[5] = {}, El = R(0), rsl = R(0);
+  ctu2_load<R, D>(b, W, Z, z);
+  // every zone, the one before the first face included, goes through the same
+  // code: a face's two states are then computed by the same instructions
+  // whichever segment or box holds the face (periodic faces 0 and n agree
+  // bitwise, and so do the faces where boxes of one domain meet)
+#pragma unroll 1
+  for (int f = fs - 1; f < fe; f++, Z += sD) {  // zone f
+    R Em, rsm, Ep, rsp;
+    ctu2_correct<R, D>(b, z, fac, Em, rsm, Ep, rsp);
+    if (f >= fs) ctu2_flux<R, D, RS>(b, W, Z, f, ql, El, rsl, z.qm, Em, rsm);
+#pragma unroll
+    for (int m = 0; m < 5; m++) ql[m] = z.qp[m];
+    El = Ep;
+    rsl = rsp;
+    if (f + 1 < fe) ctu2_load<R, D>(b, W, Z + sD, z);  // zone f+1, at most n_D
+  }
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu2_line(TableView tv, const DevBox* __restrict__ boxes,
+                                                   const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
+  if (!box_uses<R>(b)) return;
+  R* W = fields<R>(work, b);
+  switch (z_) {
+    case 0: ctu2_x<R, RS>(b, W, t_, rt[bi]); break;
+    case 1: ctu2_walk<R, 1, RS>(b, W, t_, rt[bi]); break;
+    default: ctu2_walk<R, 2, RS>(b, W, t_, rt[bi]); break;
+  }
+}
+
 // --------------------------------------------------------------------- update
 // FP32 -> FP64 on the integer pipe (the conversion instruction would occupy
 // the FP64 pipe): exact for normal floats; zero, subnormal floats (below
@@ -1365,13 +1523,15 @@ const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten"
                                            "riemann", "ctu1", "ctu2", "update"};
 
 const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
-                                           "slopes", "trace", "riemann", "ctu1", "ctu2", "line_x", "line_yz"};
+                                           "slopes", "trace", "riemann", "ctu1", "ctu2", "line_x", "line_yz",
+                                           "ctu2_line"};
 
 int default_tpb(int table) {
   switch (table) {
     case TB_TRACE:
     case TB_LINE_X:
     case TB_LINE_YZ:
+    case TB_CTU2_LINE:
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
@@ -1404,6 +1564,9 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
       const int dd = z + 1;  // walk axis: y, then z
       return (n[0] + 2) * (n[dd == 1 ? 2 : 1] + 2) * ((n[dd] + 2 + LINE_SEG - 1) / LINE_SEG);
     }
+    case TB_CTU2_LINE:
+      if (z == 0) return n[1] * n[2] * ((n[0] + 1 + 30) / 31) * 32;
+      return n[0] * n[z == 1 ? 2 : 1] * ((n[z] + 1 + LINE_SEG - 1) / LINE_SEG);
     default: return 0;
   }
 }
@@ -1472,18 +1635,29 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
       return ts ? launch(k_ctu2<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
                 : launch(k_ctu2<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
     case TB_LINE_X:
-      return ts ? launch(k_line_x<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
-                : launch(k_line_x<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
     case TB_LINE_YZ:
-      return ts ? launch(k_line_yz<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
-                : launch(k_line_yz<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+    case TB_CTU2_LINE:
+      // the line kernels exist for FP32 boxes only (LINE_FUSED_SLOT)
+      if constexpr (Consts<R>::STORE_CONSERVED) {
+        return 0;
+      } else {
+        if (table == TB_LINE_X)
+          return ts ? launch(k_line_x<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                    : launch(k_line_x<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+        if (table == TB_LINE_YZ)
+          return ts ? launch(k_line_yz<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                    : launch(k_line_yz<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+        return ts ? launch(k_ctu2_line<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                  : launch(k_ctu2_line<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+      }
     default: return 0;
   }
 }
 
-// Stage table of one compute type, with the fused line stage standing in for
-// slopes (nothing), tracing (the line kernel) and the normal Riemann solves
-// (nothing) where it applies.
+// Stage table of one compute type, with the line kernels standing in where
+// they apply: the fused line stage for slopes (nothing), tracing (the x and
+// y/z line kernels) and the normal Riemann solves (nothing), and the zone-wise
+// CTU stage 2 for the face-wise one.
 template <typename R>
 int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
   if (line_fused(p, slot)) {
@@ -1491,6 +1665,7 @@ int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
     if (table == TB_TRACE)
       return launch_typed<R>(p, TB_LINE_X, p.tab[TB_LINE_X][slot], s) +
              launch_typed<R>(p, TB_LINE_YZ, p.tab[TB_LINE_YZ][slot], s);
+    if (table == TB_CTU2) return launch_typed<R>(p, TB_CTU2_LINE, p.tab[TB_CTU2_LINE][slot], s);
   }
   return launch_typed<R>(p, table, p.tab[table][slot], s);
 }
@@ -1559,6 +1734,7 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
     case TB_CTU2:
     case TB_LINE_X:
     case TB_LINE_YZ:
+    case TB_CTU2_LINE:
       if (slot == 0) launch_typed<double>(p, table, w, stream);
       else launch_typed<float>(p, table, w, stream);
       break;
