@@ -239,9 +239,9 @@ int hydro_use_graphs(hydro_handle* h, int enable);
  * the normal fluxes reach HBM.  The arithmetic is that of the separate stages;
  * the slope fields dq of hydro_debug_fields are then not written for those
  * boxes, and the stage time of the fused kernel is reported under "trace".
- * The final transverse correction of those boxes runs zone by zone along
- * lines as well (table "ctu2_line"): the two edge states of a zone share the
- * flux differences across it, which are then read once.
+ * Both transverse-correction stages of those boxes run zone by zone along
+ * lines as well (tables "ctu1_line" and "ctu2_line"): the two edge states of
+ * a zone share the flux differences across it, which are then read once.
  * On by default; hydro_fuse_lines(h, 0) runs the separate stages. */
 int hydro_fuse_lines(hydro_handle* h, int enable);
 

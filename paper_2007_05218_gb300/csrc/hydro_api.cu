@@ -592,17 +592,18 @@ int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries
   // pipeline order, so that every table is tuned on valid inputs
   const int order[] = {hydro::TB_FILL_X,  hydro::TB_FILL_Y,  hydro::TB_FILL_Z, hydro::TB_PRIM,
                        hydro::TB_FLATTEN, hydro::TB_SLOPES,  hydro::TB_TRACE,  hydro::TB_RIEMANN,
-                       hydro::TB_LINE_X,  hydro::TB_LINE_YZ, hydro::TB_CTU1,   hydro::TB_CTU2,
-                       hydro::TB_CTU2_LINE};
+                       hydro::TB_LINE_X,  hydro::TB_LINE_YZ, hydro::TB_CTU1,   hydro::TB_CTU1_LINE,
+                       hydro::TB_CTU2,    hydro::TB_CTU2_LINE};
   for (int t : order) {
     for (int sl = 0; sl < 2; sl++) {
       hydro::WorkTable& w = p.tab[t][sl];
       if (w.capacity == 0) continue;
       // tune what the step runs: the line table, or the three stages it replaces
       const bool fused = hydro::line_fused(p, sl);
-      const bool line = t == hydro::TB_LINE_X || t == hydro::TB_LINE_YZ || t == hydro::TB_CTU2_LINE;
+      const bool line = t == hydro::TB_LINE_X || t == hydro::TB_LINE_YZ || t == hydro::TB_CTU1_LINE ||
+                        t == hydro::TB_CTU2_LINE;
       const bool replaced = t == hydro::TB_SLOPES || t == hydro::TB_TRACE || t == hydro::TB_RIEMANN ||
-                            t == hydro::TB_CTU2;
+                            t == hydro::TB_CTU1 || t == hydro::TB_CTU2;
       if (line ? !fused : fused && replaced) continue;
       int best_tpb = w.tpb, best_order = w.order;
       float best_ms = 0.f;

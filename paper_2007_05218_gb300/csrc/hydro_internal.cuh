@@ -106,12 +106,13 @@ enum TableId : int {
   TB_LINE_X,   // fused slopes + tracing + normal Riemann solves along x (FP32 boxes)
   TB_LINE_YZ,  // the same along y (item z = 0) and z (item z = 1)
   TB_CTU2_LINE,  // CTU stage 2 by zones along lines (FP32 boxes)
+  TB_CTU1_LINE,  // CTU stage 1 by zones along lines (FP32 boxes)
   NTABLES
 };
-constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 1, 2, 3};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 1, 2, 3, 6};
 // tables of the precision-specific stage kernels exist once per compute type
 constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true,
-                                               true, true, true};
+                                               true, true, true, true};
 // the fused line stage runs for FP32 boxes only (slot 1): the FP64 stages are
 // bound by the FP64 pipe, which fusion does not relieve
 constexpr bool LINE_FUSED_SLOT[2] = {false, true};

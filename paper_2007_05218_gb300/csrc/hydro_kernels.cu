@@ -1440,6 +1440,145 @@ __global__ void __launch_bounds__(256) k_ctu2_line(TableView tv, const DevBox* _
   }
 }
 
+// ------------------------------------------------ CTU stage 1 along lines
+// Stage 1 corrects each D-edge state of a zone along one transverse axis T
+// (the ordered pair (D, T)) with the flux differences across the zone along
+// T; the zone's two edge states share them.  Zone-wise, as stage 2, one pair
+// per thread.
+
+// Zone Z's two D-edge states (raw) and the flux differences across the zone
+// along T, then both states corrected along T (FP32 boxes).
+template <typename R, int D, int T>
+struct Ctu1Zone {
+  R qm[5], qp[5], dlt[1][5];
+};
+
+template <typename R, int D, int T>
+__device__ __forceinline__ void ctu1_load(const DevBox& b, const R* __restrict__ W, long long Z,
+                                          Ctu1Zone<R, D, T>& z) {
+  const long long vs = b.vs;
+#pragma unroll
+  for (int m = 0; m < 5; m++) {
+    z.qm[m] = W[(FLD_QM + 5 * D + m) * vs + Z];
+    z.qp[m] = W[(FLD_QP + 5 * D + m) * vs + Z];
+  }
+  const R* Fb[1] = {W + (FLD_F0 + 5 * T) * vs};
+  const long long st[1] = {b.s[T]};
+  flux_deltas<R, D, 1>(Fb, st, vs, Z, z.dlt);
+}
+
+template <typename R, int D, int T>
+__device__ __forceinline__ void ctu1_correct(const DevBox& b, Ctu1Zone<R, D, T>& z, R fac, R& Em, R& rsm, R& Ep,
+                                             R& rsp) {
+  static_assert(!Consts<R>::STORE_CONSERVED, "zone-wise stage 1 runs for FP32 boxes");
+  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  R um[4], up[4];
+  conserved_of(z.qm, igm1, um);
+  conserved_of(z.qp, igm1, up);
+  const R f1[1] = {fac};
+  Em = correct_by<R, 1>(z.qm, um, z.dlt, f1, gamma, igm1, rsm);
+  Ep = correct_by<R, 1>(z.qp, up, z.dlt, f1, gamma, igm1, rsp);
+}
+
+template <typename R, int D, int T, int RS>
+__device__ __forceinline__ void ctu1_store(const DevBox& b, R* __restrict__ W, long long Z, R* qL, R EL, R rsl,
+                                           R* qR, R ER, R rsr) {
+  R Fn[5];
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * b.vs, b.vs, Z, Fn);
+}
+
+// x faces of pair (x, T): lane l of warp w in a row owns zone i = -1 + 31 w + l
+// and, for l >= 1, the face at its low side (faces 0 .. n_x); rows cover T in
+// [0, n_T) and the remaining axis in [-1, n].
+template <typename R, int T, int RS>
+__device__ __forceinline__ void ctu1_x(const DevBox& b, R* __restrict__ W, long long t, const BoxRt& rt) {
+  constexpr int U = 3 - T;  // the axis other than x and T
+  int lo[3], ext[3];
+  lo[T] = 0;
+  ext[T] = b.n[T];
+  lo[U] = -1;
+  ext[U] = b.n[U] + 2;
+  const int nx = b.n[0];
+  const int wpr = (nx + 1 + 30) / 31;
+  const long long per_row = (long long)wpr * 32;
+  if (t >= per_row * ext[1] * ext[2]) return;  // whole warps only
+  const long long row = t / per_row;
+  const int rem = (int)(t - row * per_row);
+  const int lane = rem & 31;
+  const int i = -1 + 31 * (rem >> 5) + lane;
+  const int j = lo[1] + (int)(row % ext[1]), k = lo[2] + (int)(row / ext[1]);
+  const long long Z = zone(b, min(i, nx), j, k);
+  Ctu1Zone<R, 0, T> z;
+  R ql[5], Em, Ep, rsm, rsp;
+  ctu1_load<R, 0, T>(b, W, Z, z);
+  ctu1_correct<R, 0, T>(b, z, Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0), Em, rsm, Ep, rsp);
+#pragma unroll
+  for (int m = 0; m < 5; m++) ql[m] = __shfl_up_sync(0xffffffffu, z.qp[m], 1);
+  const R El = __shfl_up_sync(0xffffffffu, Ep, 1), rsl = __shfl_up_sync(0xffffffffu, rsp, 1);
+  if (lane == 0 || i > nx) return;
+  ctu1_store<R, 0, T, RS>(b, W, Z, ql, El, rsl, z.qm, Em, rsm);
+}
+
+// y and z faces of pair (D, T): a thread walks LINE_SEG faces of one column
+// (x and the other transverse axis: T in [0, n_T), the remaining one in
+// [-1, n]); every zone goes through the same code, the one before the first
+// face included.
+template <typename R, int D, int T, int RS>
+__device__ __forceinline__ void ctu1_walk(const DevBox& b, R* __restrict__ W, long long t, const BoxRt& rt) {
+  constexpr int O = D == 1 ? 2 : 1;  // the transverse axis other than x
+  constexpr int U = 3 - D - T;       // the transverse axis other than T
+  int lo[3], ext[3];
+  lo[T] = 0;
+  ext[T] = b.n[T];
+  lo[U] = -1;
+  ext[U] = b.n[U] + 2;
+  const int nd = b.n[D];
+  const int nseg = (nd + 1 + LINE_SEG - 1) / LINE_SEG;
+  if (t >= (long long)ext[0] * ext[O] * nseg) return;
+  const long long rest = t / ext[0];
+  int c[3];
+  c[0] = lo[0] + (int)(t - rest * ext[0]);
+  c[O] = lo[O] + (int)(rest % ext[O]);
+  const int fs = (int)(rest / ext[O]) * LINE_SEG;
+  const int fe = min(fs + LINE_SEG, nd + 1);  // faces [fs, fe), within [0, n_D]
+  c[D] = fs - 1;
+  const long long sD = b.s[D];
+  long long Z = zone(b, c[0], c[1], c[2]);
+  const R fac = Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0);
+  Ctu1Zone<R, D, T> z;
+  R ql[5] = {}, El = R(0), rsl = R(0);
+  ctu1_load<R, D, T>(b, W, Z, z);
+#pragma unroll 1
+  for (int f = fs - 1; f < fe; f++, Z += sD) {  // zone f
+    R Em, Ep, rsm, rsp;
+    ctu1_correct<R, D, T>(b, z, fac, Em, rsm, Ep, rsp);
+    if (f >= fs) ctu1_store<R, D, T, RS>(b, W, Z, ql, El, rsl, z.qm, Em, rsm);
+#pragma unroll
+    for (int m = 0; m < 5; m++) ql[m] = z.qp[m];
+    El = Ep;
+    rsl = rsp;
+    if (f + 1 < fe) ctu1_load<R, D, T>(b, W, Z + sD, z);  // zone f+1, at most n_D
+  }
+}
+
+// work item z = pair slot (xy xz yx yz zx zy)
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu1_line(TableView tv, const DevBox* __restrict__ boxes,
+                                                   const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  LOCATE(tv)
+  if (!box_uses<R>(b)) return;
+  R* W = fields<R>(work, b);
+  switch (z_) {
+    case 0: ctu1_x<R, 1, RS>(b, W, t_, rt[bi]); break;
+    case 1: ctu1_x<R, 2, RS>(b, W, t_, rt[bi]); break;
+    case 2: ctu1_walk<R, 1, 0, RS>(b, W, t_, rt[bi]); break;
+    case 3: ctu1_walk<R, 1, 2, RS>(b, W, t_, rt[bi]); break;
+    case 4: ctu1_walk<R, 2, 0, RS>(b, W, t_, rt[bi]); break;
+    default: ctu1_walk<R, 2, 1, RS>(b, W, t_, rt[bi]); break;
+  }
+}
+
 // --------------------------------------------------------------------- update
 // FP32 -> FP64 on the integer pipe (the conversion instruction would occupy
 // the FP64 pipe): exact for normal floats; zero, subnormal floats (below
@@ -1524,7 +1663,7 @@ const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten"
 
 const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
                                            "slopes", "trace", "riemann", "ctu1", "ctu2", "line_x", "line_yz",
-                                           "ctu2_line"};
+                                           "ctu2_line", "ctu1_line"};
 
 int default_tpb(int table) {
   switch (table) {
@@ -1532,6 +1671,7 @@ int default_tpb(int table) {
     case TB_LINE_X:
     case TB_LINE_YZ:
     case TB_CTU2_LINE:
+    case TB_CTU1_LINE:
     case TB_RIEMANN:
     case TB_CTU1:
     case TB_CTU2:
@@ -1567,6 +1707,16 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
     case TB_CTU2_LINE:
       if (z == 0) return n[1] * n[2] * ((n[0] + 1 + 30) / 31) * 32;
       return n[0] * n[z == 1 ? 2 : 1] * ((n[z] + 1 + LINE_SEG - 1) / LINE_SEG);
+    case TB_CTU1_LINE: {
+      const int dd = z / 2, r = z % 2;  // pair slot -> (D, T)
+      const int tt = r == 0 ? (dd == 0 ? 1 : 0) : (dd == 2 ? 1 : 2);
+      const int uu = 3 - dd - tt;
+      long long ext[3];
+      ext[tt] = n[tt];
+      ext[uu] = n[uu] + 2;
+      if (dd == 0) return ext[1] * ext[2] * ((n[0] + 1 + 30) / 31) * 32;
+      return ext[0] * ext[dd == 1 ? 2 : 1] * ((n[dd] + 1 + LINE_SEG - 1) / LINE_SEG);
+    }
     default: return 0;
   }
 }
@@ -1637,6 +1787,7 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
     case TB_LINE_X:
     case TB_LINE_YZ:
     case TB_CTU2_LINE:
+    case TB_CTU1_LINE:
       // the line kernels exist for FP32 boxes only (LINE_FUSED_SLOT)
       if constexpr (Consts<R>::STORE_CONSERVED) {
         return 0;
@@ -1647,6 +1798,9 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
         if (table == TB_LINE_YZ)
           return ts ? launch(k_line_yz<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
                     : launch(k_line_yz<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
+        if (table == TB_CTU1_LINE)
+          return ts ? launch(k_ctu1_line<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
+                    : launch(k_ctu1_line<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
         return ts ? launch(k_ctu2_line<R, HYDRO_RIEMANN_TWO_SHOCK>, w, s, p.dboxes, rt, p.work)
                   : launch(k_ctu2_line<R, HYDRO_RIEMANN_HLLC>, w, s, p.dboxes, rt, p.work);
       }
@@ -1657,7 +1811,7 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
 // Stage table of one compute type, with the line kernels standing in where
 // they apply: the fused line stage for slopes (nothing), tracing (the x and
 // y/z line kernels) and the normal Riemann solves (nothing), and the zone-wise
-// CTU stage 2 for the face-wise one.
+// CTU stages for the face-wise ones.
 template <typename R>
 int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
   if (line_fused(p, slot)) {
@@ -1665,6 +1819,7 @@ int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
     if (table == TB_TRACE)
       return launch_typed<R>(p, TB_LINE_X, p.tab[TB_LINE_X][slot], s) +
              launch_typed<R>(p, TB_LINE_YZ, p.tab[TB_LINE_YZ][slot], s);
+    if (table == TB_CTU1) return launch_typed<R>(p, TB_CTU1_LINE, p.tab[TB_CTU1_LINE][slot], s);
     if (table == TB_CTU2) return launch_typed<R>(p, TB_CTU2_LINE, p.tab[TB_CTU2_LINE][slot], s);
   }
   return launch_typed<R>(p, table, p.tab[table][slot], s);
@@ -1735,6 +1890,7 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
     case TB_LINE_X:
     case TB_LINE_YZ:
     case TB_CTU2_LINE:
+    case TB_CTU1_LINE:
       if (slot == 0) launch_typed<double>(p, table, w, stream);
       else launch_typed<float>(p, table, w, stream);
       break;

@@ -50,9 +50,9 @@ def test_autotune_keeps_state_and_results(precision):
         np.testing.assert_array_equal(x, y)
     names = {t[0] for t in tuned}
     # FP32 boxes run the fused line stage in place of slopes, tracing and the normal solves
-    staged = ({"slopes", "trace", "riemann", "ctu2"} if precision == hydro.HYDRO_FP64
-              else {"line_x", "line_yz", "ctu2_line"})
-    assert {"prim", "ctu1"} | staged <= names
+    staged = ({"slopes", "trace", "riemann", "ctu1", "ctu2"} if precision == hydro.HYDRO_FP64
+              else {"line_x", "line_yz", "ctu1_line", "ctu2_line"})
+    assert {"prim"} | staged <= names
     assert all(t[2] in (64, 128, 256) and t[3] in (0, 1) and t[4] > 0 for t in tuned)
 
 
