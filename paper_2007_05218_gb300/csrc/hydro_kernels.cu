@@ -715,10 +715,10 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // Toro, Spruce & Speares 1994 with Roe-averaged bounds (Batten et al. 1997),
 // Davis bounds when the Roe sound speed is not real.  Only the star state on
 // the side of the contact that contains x/t = 0 is formed.  All square roots
-// and reciprocals come from two reciprocal square roots per side (sqrt(rho),
-// 1/rho, c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed)
+// and reciprocals come from two reciprocal square roots per side (sqrt(rho)
+// and 1/rho, c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed)
 // and three reciprocals; wave-speed min/max and sign tests run on the integer
-// pipe.
+// pipe in FP64.
 template <typename R>
 __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R* F) {
   const R gm1 = gamma - R(1);
@@ -730,7 +730,6 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
     rsr = nr_rsqrt(rr);
   }
   const R sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
-  const R irl = rsl * rsl, irr = rsr * rsr;          // 1/rho
   const R gpl = gamma * pl, gpr = gamma * pr;
   const R cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
   const R iw = nr_rcp(sl + sr);
@@ -738,7 +737,8 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const R ut = wgl * ul + wgr * ur;
   const R vt = wgl * vl + wgr * vr;
   const R wt = wgl * wl + wgr * wr;
-  const R Ht = wgl * ((El + pl) * irl) + wgr * ((Er + pr) * irr);
+  // Roe enthalpy: sum of w_K (E_K + p_K) / rho_K = sum of (E_K + p_K) / sqrt(rho_K), times iw
+  const R Ht = ((El + pl) * rsl + (Er + pr) * rsr) * iw;
   const R ct2 = gm1 * (Ht - R(0.5) * (ut * ut + vt * vt + wt * wt));
   R SL, SR;
   if (is_pos(ct2)) {
@@ -754,7 +754,7 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const bool left = is_nonneg(Ss);
   const R rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
   const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
-  const R irK = left ? irl : irr;
+  const R rsK = left ? rsl : rsr;
   const R mu = rK * uK;
   F[0] = mu;
   F[1] = mu * uK + pK;
@@ -765,7 +765,7 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
     const R den = SK - Ss;
     const R r = nr_rcp(mK * den);
     const R fac = mK * mK * r;
-    const R eK = EK * irK + (Ss - uK) * (Ss + pK * den * r);
+    const R eK = EK * (rsK * rsK) + (Ss - uK) * (Ss + pK * den * r);
     F[0] += SK * (fac - rK);
     F[1] += SK * (fac * Ss - mu);
     F[4] += SK * (fac * eK - EK);
