@@ -536,17 +536,20 @@ __device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
 
 // CW84 monotonicity limiter of the parabola of zone value a0 between face
 // values L, Rt, then the flattening blend with coefficient f.
+// With x = a0 - L and y = Rt - a0 of one sign, CW84's overshoot tests
+// dA (a0 - (L + Rt)/2) > dA^2/6 and -dA^2/6 > dA (a0 - (L + Rt)/2), dA = x + y,
+// are |x| > 2|y| and |y| > 2|x|; each replaced edge equals the old one on the
+// boundary of its test, so the limiter is continuous there.
 template <typename R>
 __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
-  if (!same_sign(Rt - a0, a0 - L)) {
+  const R x = a0 - L, y = Rt - a0;
+  if (!same_sign(y, x)) {
     L = a0;
     Rt = a0;
   } else {
-    const R dA = Rt - L;
-    const R t1 = dA * (a0 - R(0.5) * (L + Rt));
-    const R t2 = dA * dA * R(1.0 / 6.0);
-    if (dgt(t1, t2)) L = R(3) * a0 - R(2) * Rt;
-    else if (dgt(-t2, t1)) Rt = R(3) * a0 - R(2) * L;
+    const R ax = fabs(x), ay = fabs(y);
+    if (dgt(ax, R(2) * ay)) L = a0 - R(2) * y;
+    else if (dgt(ay, R(2) * ax)) Rt = a0 + R(2) * x;
   }
   if (is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
