@@ -35,6 +35,9 @@ CASES = {
     "density_wave": (lambda: inputs.density_wave((24, 20, 16), seed=3), 30),
     "sedov": (lambda: inputs.sedov((24, 24, 24), seed=2), 30),
     "kelvin_helmholtz": (lambda: inputs.kelvin_helmholtz((24, 32, 16), seed=4), 30),
+    "minimum_box_4cubed": (lambda: inputs.density_wave((4, 4, 4), seed=5), 20),
+    "long_thin_x": (lambda: inputs.kelvin_helmholtz((300, 4, 6), seed=6), 20),
+    "long_thin_y": (lambda: inputs.density_wave((5, 130, 4), seed=7), 20),
 }
 
 

@@ -49,6 +49,9 @@ CASES = {
     "kelvin_helmholtz_reflect_y": lambda: inputs.kelvin_helmholtz((12, 16, 10), seed=4),
     "uniform_outflow": lambda: inputs.uniform((8, 9, 10), bc="outflow"),
     "uniform_reflect": lambda: inputs.uniform((7, 6, 5), vel=(0.0, 0.0, 0.0), bc="reflect"),
+    "minimum_box_4cubed": lambda: inputs.density_wave((4, 4, 4), seed=5),
+    "long_thin_x": lambda: inputs.kelvin_helmholtz((300, 4, 6), seed=6),
+    "long_thin_z": lambda: inputs.density_wave((4, 6, 200), seed=7),
 }
 
 
