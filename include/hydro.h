@@ -156,10 +156,12 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
  * fluxes f1[6][5] for the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes
  * f[3][5]; limited slopes dq[3][5] of the normal-frame variables of each axis;
  * conserved momenta (normal frame) and total energy of the left- and right-edge
- * states, um[3][4] and up[3][4].
+ * states, um[3][4] and up[3][4] (HYDRO_FP64 boxes only: HYDRO_MIXED boxes
+ * rebuild them from the primitive edge states where they are needed).
  * Fluxes are conserved-variable components; the flux through the low face of
  * zone (i,j,k) along d is stored at (i,j,k).  Values are defined only where
- * the step computes them. */
+ * the step computes them (see also hydro_fuse_lines and hydro_set_method for
+ * what dq holds). */
 int hydro_debug_fields(const hydro_box_desc* d, int nboxes, int box, int64_t* offset_bytes, int32_t* nfields,
                        int32_t* elem_bytes);
 
