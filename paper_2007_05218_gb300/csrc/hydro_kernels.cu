@@ -361,27 +361,36 @@ __device__ __forceinline__ float vl_slope<float>(float am, float a0, float ap) {
   return copysignf(fminf(fabsf(dc), fminf(2.0f * fabsf(dl), 2.0f * fabsf(dr))), dc);
 }
 
-// FP64 form: the halving and doublings are exponent shifts of the bit
-// patterns, so the FP64 pipe only sees the three subtractions.  A shift is
-// exact only while the number and its result stay normal; differences near
-// the subnormal range (numerical tails ahead of a front decay that far) or
-// the overflow threshold take the multiplies instead.
+// FP64 form: the halving and doublings are exponent changes of the bit
+// patterns and the sign tests and minimum are integer comparisons, all on
+// 32-bit halves (a double's sign, exponent and top mantissa bits sit in its
+// high word), so the FP64 pipe only sees the three subtractions.  A changed
+// exponent is exact only while the number and its result stay normal;
+// differences near the subnormal range (numerical tails ahead of a front decay
+// that far) or the overflow threshold take the multiplies instead.
+__device__ __forceinline__ bool hw_nonzero(int hi, int lo) { return ((hi & 0x7fffffff) | lo) != 0; }
+
 template <>
 __device__ __forceinline__ double vl_slope<double>(double am, double a0, double ap) {
   const double dl = a0 - am, dr = ap - a0;
-  if (!same_sign(dl, dr)) return 0.0;
-  constexpr long long ONE_EXP = 1LL << 52, MAG = 0x7fffffffffffffffLL;
+  const int hl = __double2hiint(dl), ll = __double2loint(dl);
+  const int hr = __double2hiint(dr), lr = __double2loint(dr);
+  if ((hl ^ hr) < 0 || !hw_nonzero(hl, ll) || !hw_nonzero(hr, lr)) return 0.0;  // not of one sign
   const double sum = ap - am;
-  const long long c = dbits(sum), l = dbits(dl) & MAG, r = dbits(dr) & MAG;
-  const long long ec = (c >> 52) & 0x7ff, el = l >> 52, er = r >> 52;
+  const int hc = __double2hiint(sum), lc = __double2loint(sum);
+  const int ec = (hc >> 20) & 0x7ff, el = (hl >> 20) & 0x7ff, er = (hr >> 20) & 0x7ff;
   if (ec < 2 || el < 1 || er < 1 || el > 0x7fd || er > 0x7fd) {
     const double dc = 0.5 * sum;
     return copysign(fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr))), dc);
   }
-  long long m = (c & MAG) - ONE_EXP;  // |ap - am| / 2
-  m = min(m, l + ONE_EXP);            // 2 |dl|
-  m = min(m, r + ONE_EXP);            // 2 |dr|
-  return from_bits(m | (c & ~MAG));   // sign of ap - am
+  constexpr int ONE_EXP = 1 << 20;
+  // magnitudes as (high, low) pairs: |sum|/2, 2|dl|, 2|dr|; the smallest wins
+  unsigned mh = (unsigned)((hc & 0x7fffffff) - ONE_EXP), ml = (unsigned)lc;
+  const unsigned h2 = (unsigned)((hl & 0x7fffffff) + ONE_EXP), l2 = (unsigned)ll;
+  if (h2 < mh || (h2 == mh && l2 < ml)) { mh = h2; ml = l2; }
+  const unsigned h3 = (unsigned)((hr & 0x7fffffff) + ONE_EXP), l3 = (unsigned)lr;
+  if (h3 < mh || (h3 == mh && l3 < ml)) { mh = h3; ml = l3; }
+  return __hiloint2double((int)(mh | ((unsigned)hc & 0x80000000u)), (int)ml);  // sign of ap - am
 }
 
 // Limited slopes of the five normal-frame variables of axis D, once per zone
