@@ -251,13 +251,18 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       sbits = (unsigned long long)__double_as_longlong(s);
     }
   }
-  // non-negative doubles order like their bit patterns: reduce as integers
+  // non-negative doubles order like their bit patterns: reduce as integers,
+  // in 32-bit halves
+  unsigned hs = (unsigned)(sbits >> 32), ls = (unsigned)sbits;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    unsigned long long o = __shfl_xor_sync(0xffffffffu, sbits, off);
-    sbits = o > sbits ? o : sbits;
+    const unsigned ho = __shfl_xor_sync(0xffffffffu, hs, off), lo = __shfl_xor_sync(0xffffffffu, ls, off);
+    if (ho > hs || (ho == hs && lo > ls)) {
+      hs = ho;
+      ls = lo;
+    }
   }
-  if ((threadIdx.x & 31) == 0 && sbits) atomicMax(&rt[bi].smax, sbits);
+  if ((threadIdx.x & 31) == 0 && (hs | ls)) atomicMax(&rt[bi].smax, ((unsigned long long)hs << 32) | ls);
 }
 
 __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, int nboxes,
@@ -1598,11 +1603,11 @@ __global__ void __launch_bounds__(256) k_ctu1_line(TableView tv, const DevBox* _
 // so conservation is untouched.
 __device__ __forceinline__ double widen(float x) {
   const unsigned int f = __float_as_uint(x);
-  const unsigned int e = (f >> 23) & 0xffu;
-  const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
-  if (e == 0u) return __longlong_as_double((long long)sign);
-  const unsigned long long mag = ((unsigned long long)(f & 0x7fffffffu) << 29) + (896ull << 52);
-  return __longlong_as_double((long long)(sign | mag));
+  const unsigned int sign = f & 0x80000000u;
+  if ((f & 0x7f800000u) == 0u) return __hiloint2double((int)sign, 0);
+  // exponent rebias 127 -> 1023 (+896) and mantissa 23 -> 52 bits, in 32-bit halves
+  const unsigned int hi = sign | (((f & 0x7fffffffu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(f << 29));
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 
