@@ -17,9 +17,11 @@
 // FP32 (float, mixed precision): the CUDA single-precision reciprocal and
 // square root (correctly rounded) and rsqrtf (within 2 ulp).
 //
-// Sign tests and min/max on the bit patterns run on the integer pipe and give
-// the same answers as floating-point comparisons for every finite non-NaN
-// input (products that underflow to zero aside).
+// FP64 sign tests and min/max work on the bit patterns, in their two 32-bit
+// halves (64-bit integer operations on the patterns were measured to cost
+// FP64-pipe time), and give the same answers as floating-point comparisons for
+// every finite non-NaN input (products that underflow to zero aside).  FP32
+// uses the native instructions.  The generic templates state the semantics.
 #pragma once
 
 namespace hydro {
