@@ -314,13 +314,16 @@ __global__ void __launch_bounds__(256) k_dt_shared(const DevBox* __restrict__ bo
 
 // ---------------------------------------------------------------- flattening
 template <typename R>
+// (comparisons and min/max through the helpers: exact, and off the FP64 pipe;
+// the ratio dp1/dp2 only enters the clamped linear part, so the refined
+// reciprocal's rounding moves the coefficient by rounding alone)
 __device__ __forceinline__ R flat_tilde(const R* __restrict__ p, const R* __restrict__ un, long long Z, long long s) {
   const R pp = p[Z + s], pm = p[Z - s];
   const R dp1 = pp - pm;
-  if (!(fabs(dp1) > R(FLAT_EPS) * fmin(pp, pm)) || !(un[Z - s] - un[Z + s] > R(0))) return R(0);
+  if (!dgt(R(fabs(dp1)), R(FLAT_EPS) * dmin(pp, pm)) || !is_pos(un[Z - s] - un[Z + s])) return R(0);
   const R dp2 = p[Z + 2 * s] - p[Z - 2 * s];
-  if (dp2 == R(0)) return R(0);
-  return fmin(R(1), fmax(R(0), R(FLAT_OMEGA2) * (dp1 / dp2 - R(FLAT_OMEGA1))));
+  if (!is_pos(fabs(dp2))) return R(0);
+  return dmin(R(1), dmax(R(0), R(FLAT_OMEGA2) * (dp1 * nr_rcp(dp2) - R(FLAT_OMEGA1))));
 }
 
 template <typename R>
@@ -338,8 +341,8 @@ __global__ void __launch_bounds__(256) k_flatten(TableView tv, const DevBox* __r
   for (int d = 0; d < 3; d++) {
     const R* un = W + (1 + d) * b.vs;
     const long long s = b.s[d];
-    const long long sh = p[Z + s] - p[Z - s] >= R(0) ? s : -s;
-    f = fmax(f, fmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s)));
+    const long long sh = is_nonneg(p[Z + s] - p[Z - s]) ? s : -s;
+    f = dmax(f, dmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s)));
   }
   W[FLD_CHI * b.vs + Z] = f;
 }
