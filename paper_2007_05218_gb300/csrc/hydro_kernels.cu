@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
     const long long vs = b.vs;
     const double* U = state + b.state_off;
     double rho = U[Z];
-    if (rho < SMALL_DENS) rho = SMALL_DENS;
+    if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
     double u, v, w, p, cs;
     if constexpr (EXACT) {
       u = __ddiv_rn(U[vs + Z], rho);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
       const double kin = __dmul_rn(__dmul_rn(0.5, rho), uu);
       p = __dmul_rn(__dsub_rn(b.gamma, 1.0), __dsub_rn(U[4 * vs + Z], kin));
-      if (p < SMALL_PRES) p = SMALL_PRES;
+      if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
       cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(b.gamma, p), rho));
     } else {
       const double ir = nr_rcp(rho);
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       v = U[2 * vs + Z] * ir;
       w = U[3 * vs + Z] * ir;
       p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
-      if (p < SMALL_PRES) p = SMALL_PRES;
+      if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
       cs = nr_sqrt(b.gamma * p * ir);
     }
     if (b.precision == HYDRO_FP64) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       W[FLD_C * vs + Z] = (float)cs;
     }
     if (c[0] >= 0 && c[0] < b.n[0] && c[1] >= 0 && c[1] < b.n[1] && c[2] >= 0 && c[2] < b.n[2]) {
-      double s = fmax(fmax((fabs(u) + cs) * b.idx[0], (fabs(v) + cs) * b.idx[1]), (fabs(w) + cs) * b.idx[2]);
+      double s = dmax(dmax((fabs(u) + cs) * b.idx[0], (fabs(v) + cs) * b.idx[1]), (fabs(w) + cs) * b.idx[2]);
       sbits = (unsigned long long)__double_as_longlong(s);
     }
   }
@@ -1648,7 +1648,11 @@ __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __re
   // rho > 0 and p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0, i.e. 2 rho E > |m|^2:
   // no reciprocal; a NaN fails the tests
   const double m2 = nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3];
-  if (!(nu[0] > 0.0) || !(2.0 * nu[0] * nu[4] - m2 > 0.0)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+  // is_pos reads bit patterns, under which a NaN with a clear sign bit counts
+  // as positive; e2 != e2 catches every NaN (one in the density, the energy or
+  // a momentum makes e2 NaN)
+  const double e2 = 2.0 * nu[0] * nu[4] - m2;
+  if (!is_pos(nu[0]) || !is_pos(e2) || e2 != e2) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
 }
 
 // ----------------------------------------------------- host staging transfers
