@@ -1,11 +1,14 @@
-// Stage kernels of the unsplit PPM/CTU/HLLC update, one kernel per stage with
-// the intermediates in HBM scratch.
+// Stage kernels of the unsplit PPM/CTU update, one kernel per stage with the
+// intermediates in HBM scratch.
 //
 // Design for GB300: the update costs thousands of floating-point operations
 // per zone and GB300's FP64 pipe is narrow, while HBM bandwidth is plentiful.
 // So every quantity is computed once and parked in HBM rather than recomputed
 // by neighbouring threads: the stage kernels read their stencil from scratch
-// fields laid out like the state (x fastest, coalesced across a warp).
+// fields laid out like the state (x fastest, coalesced across a warp).  For
+// FP32 boxes, where the stages are bound by memory traffic instead, four
+// line kernels (listed below) fuse several stages along one axis and keep the
+// stencil in registers.
 //
 // Precision.  The state, the dt reduction and the flux-divergence update are
 // always FP64.  The reconstruction, tracing, CTU corrections and Riemann
@@ -21,12 +24,20 @@
 //   k_prim       conserved -> primitive + EOS (FP64); per-box max signal speed
 //   k_dt         dt = cfl / max((|u_d|+c)/dx_d)
 //   k_flatten    CW84 §4 shock flattening coefficient (max over directions)
-//   k_slopes     CW84 limited slopes, once per zone and axis
-//   k_trace      CW84 PPM parabolas + characteristic tracing -> face states
-//   k_riemann    HLLC normal fluxes F0_d on the extended face region
-//   k_ctu1       3D CTU stage 1: dt/(3dx_e) transverse corrections + HLLC
-//   k_ctu2       3D CTU stage 2: dt/(2dx) corrections + HLLC -> final fluxes
+//   k_slopes     CW84 limited slopes, once per zone and axis (none for CS08)
+//   k_trace      PPM parabolas (CW84 or CS08 limiter) + characteristic
+//                tracing -> face states
+//   k_riemann    normal fluxes F0_d on the extended face region (HLLC or the
+//                two-shock solver, as for every Riemann solve below)
+//   k_ctu1       3D CTU stage 1: dt/(3dx_e) transverse corrections + solves
+//   k_ctu2       3D CTU stage 2: dt/(2dx) corrections + solves -> final fluxes
 //   k_update     conservative flux-divergence update (FP64) + physicality flag
+// FP32 boxes (unless line fusion is switched off) replace the middle stages:
+//   k_line_x     slopes + trace + normal solve along x, one warp per x-line
+//   k_line_yz    the same along y or z, threads walking a column segment
+//   k_ctu1_line  CTU stage 1, zone-wise: each zone's flux differences loaded
+//                once for both of its faces
+//   k_ctu2_line  CTU stage 2, zone-wise in the same way
 #include <algorithm>
 #include <cmath>
 #include <vector>
