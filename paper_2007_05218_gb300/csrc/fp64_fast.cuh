@@ -17,11 +17,12 @@
 // FP32 (float, mixed precision): the CUDA single-precision reciprocal and
 // square root (correctly rounded) and rsqrtf (within 2 ulp).
 //
-// FP64 sign tests and min/max work on the bit patterns, in their two 32-bit
-// halves (64-bit integer operations on the patterns were measured to cost
-// FP64-pipe time), and give the same answers as floating-point comparisons for
-// every finite non-NaN input (products that underflow to zero aside).  FP32
-// uses the native instructions.  The generic templates state the semantics.
+// FP64 sign tests, min/max, halvings and the |x| > 2|y| test work on the bit
+// patterns, in their two 32-bit halves (64-bit integer operations on the
+// patterns were measured to cost FP64-pipe time), and give the same answers as
+// floating-point operations for every finite non-NaN input (products that
+// underflow to zero aside).  FP32 uses the native instructions.  The generic
+// templates state the semantics.
 #pragma once
 
 namespace hydro {
@@ -92,6 +93,12 @@ __device__ __forceinline__ R dmax(R a, R b) { return dkey(a) >= dkey(b) ? a : b;
 // a > b
 template <typename R>
 __device__ __forceinline__ bool dgt(R a, R b) { return dkey(a) > dkey(b); }
+// x / 2, correctly rounded
+template <typename R>
+__device__ __forceinline__ R half_of(R x) { return R(0.5) * x; }
+// |x| > 2 |y|
+template <typename R>
+__device__ __forceinline__ bool abs_gt_twice(R x, R y) { return fabs(x) > R(2) * fabs(y); }
 
 // FP64 forms on the two 32-bit halves of each double (sign, exponent and top
 // mantissa bits in the high word): 64-bit integer operations on the bit
@@ -131,6 +138,43 @@ template <>
 __device__ __forceinline__ double dmin<double>(double a, double b) { return dgt(a, b) ? b : a; }
 template <>
 __device__ __forceinline__ double dmax<double>(double a, double b) { return dgt(b, a) ? b : a; }
+// x / 2 without an FP64 instruction.  For 2^-1021 <= |x| < inf it is an
+// exponent decrement of the high word.  Below that range the magnitude bits
+// (exponent field 0 or 1) read as an integer M give |x| = M 2^-1074, so x / 2
+// is the pattern M / 2 rounded half to even; zero stays zero.  Infinities and
+// NaN are returned unchanged.
+template <>
+__device__ __forceinline__ double half_of<double>(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned mh = (unsigned)hi & 0x7fffffffu;
+  constexpr unsigned E2 = 2u << 20, INF = 0x7ff00000u;
+  if (mh - E2 < INF - E2) return __hiloint2double(hi - (1 << 20), (int)lo);
+  if (mh >= INF) return x;
+  const unsigned ql = (lo >> 1) | (mh << 31), qh = mh >> 1;
+  const unsigned rl = ql + (lo & ql & 1u);  // a dropped half rounds an odd result up
+  const unsigned rh = qh + (rl < ql ? 1u : 0u);
+  return __hiloint2double((int)(rh | ((unsigned)hi & 0x80000000u)), (int)rl);
+}
+// |x| > 2 |y| for finite x, y, on the magnitude bits: 2|y| is an exponent
+// increment of a normal |y| and the magnitude pattern doubled for a
+// subnormal one (which is exact, also where it becomes normal); a normal |y|
+// of 2^1023 or more makes 2|y| overflow, which no finite |x| exceeds.
+template <>
+__device__ __forceinline__ bool abs_gt_twice<double>(double x, double y) {
+  const unsigned hx = (unsigned)__double2hiint(x) & 0x7fffffffu, lx = (unsigned)__double2loint(x);
+  const unsigned hy = (unsigned)__double2hiint(y) & 0x7fffffffu, ly = (unsigned)__double2loint(y);
+  unsigned h2, l2;
+  if (hy >= (1u << 20)) {
+    if (hy >= 0x7fe00000u) return false;
+    h2 = hy + (1u << 20);
+    l2 = ly;
+  } else {
+    h2 = (hy << 1) | (ly >> 31);
+    l2 = ly << 1;
+  }
+  return hx > h2 || (hx == h2 && lx > l2);
+}
 
 // FP32 keeps its comparisons and min/max native: the FP32 units are not the
 // scarce resource there, and one native instruction replaces the several

@@ -556,10 +556,11 @@ __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __re
 // dm1, d0, dp1: interface values (CW84 eq. 1.6), monotonicity limiter
 // (eq. 1.10) with its tests on the integer pipe, then flattening by f.
 // 4th-order value at the face between zones of values am1, a0 and limited
-// slopes dm1, d0 (CW84 eq. 1.6).
+// slopes dm1, d0 (CW84 eq. 1.6), as (am1 + a0)/2 - (d0 - dm1)/6 with the
+// halving exact (on the integer pipe in FP64).
 template <typename R>
 __device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
-  return am1 + R(0.5) * (a0 - am1) - (d0 - dm1) * R(1.0 / 6.0);
+  return half_of(am1 + a0) - (d0 - dm1) * R(1.0 / 6.0);
 }
 
 // CW84 monotonicity limiter of the parabola of zone value a0 between face
@@ -574,10 +575,10 @@ __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   if (!same_sign(y, x)) {
     L = a0;
     Rt = a0;
-  } else {
-    const R ax = fabs(x), ay = fabs(y);
-    if (dgt(ax, R(2) * ay)) L = a0 - R(2) * y;
-    else if (dgt(ay, R(2) * ax)) Rt = a0 + R(2) * x;
+  } else if (abs_gt_twice(x, y)) {
+    L = a0 - R(2) * y;
+  } else if (abs_gt_twice(y, x)) {
+    Rt = a0 + R(2) * x;
   }
   if (is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
@@ -600,7 +601,7 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
   W[(base + 4 * D + 0) * vs + Z] = q[0] * q[1];
   W[(base + 4 * D + 1) * vs + Z] = q[0] * q[2];
   W[(base + 4 * D + 2) * vs + Z] = q[0] * q[3];
-  W[(base + 4 * D + 3) * vs + Z] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  W[(base + 4 * D + 3) * vs + Z] = q[4] * igm1 + half_of(q[0]) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
 // Characteristic tracing of one zone along one axis (Miller & Colella 2002
@@ -610,45 +611,50 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
 // left-edge state (side 0) to sink(side, q[5]) as soon as each is formed.
 template <typename R, typename Sink>
 __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R dtdx, Sink&& sink) {
-  R dA[5], a6[5];
+  // The parabola's dA = aR - aL and a6 = 6 (a0 - (aL + aR)/2) (CW84 §1); the
+  // factor 6 of a6 is carried by h2 below, so c6 holds a6 / 6.  For a wave
+  // of speed lambda, sigma = |lambda| dt/dx, the average of the parabola over
+  // the wave's domain of dependence at an edge is edge -+ h1 (dA -+ h2 c6)
+  // with h1 = sigma / 2 and h2 = 6 (1 - 2 sigma / 3) = 6 - 4 sigma.
+  R dA[5], c6[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     dA[m] = aR[m] - aL[m];
-    a6[m] = R(6) * (a0[m] - R(0.5) * (aL[m] + aR[m]));
+    c6[m] = a0[m] - half_of(aL[m] + aR[m]);
   }
   const R rho = a0[0], u = a0[1];
   const R ic = nr_rcp(cs);
-  const R rc = R(0.5) * rho * ic;   // rho / 2c
-  const R i2c2 = R(0.5) * ic * ic;  // 1 / 2c^2
+  const R rc = rho * half_of(ic);   // rho / 2c
   const R ic2 = ic * ic;            // 1 / c^2
+  const R i2c2 = half_of(ic2);      // 1 / 2c^2
   const R cr = cs * nr_rcp(rho);    // c / rho
   const R c2 = cs * cs;
   const R lm = u - cs, lp = u + cs;
-  const R two3 = R(2.0 / 3.0);
+  const R hdt = half_of(dtdx), fdt = R(4) * dtdx;
 
   R out[5];
   // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
   if (is_pos(lp)) {
-    R sg = lp * dtdx, h1 = R(0.5) * sg, h2 = R(1) - sg * two3;
+    R h1 = lp * hdt, h2 = R(6) - lp * fdt;
     R ref[5];
 #pragma unroll
-    for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * a6[m]);
+    for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * c6[m]);
     R bm = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
     if (is_pos(lm)) {
-      sg = lm * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
-      const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * a6[1]));
-      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      h1 = lm * hdt; h2 = R(6) - lm * fdt;
+      const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * c6[1]));
+      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
       bm = -rc * du + i2c2 * dp;
     }
     if (is_pos(u)) {
-      sg = u * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
-      const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * a6[0]));
-      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * a6[4]));
+      h1 = u * hdt; h2 = R(6) - u * fdt;
+      const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * c6[0]));
+      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
       b0 = dr - ic2 * dp;
-      out[2] = aR[2] - h1 * (dA[2] - h2 * a6[2]);
-      out[3] = aR[3] - h1 * (dA[3] - h2 * a6[3]);
+      out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
+      out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
     }
     out[0] = ref[0] - (bm + b0);
     out[1] = ref[1] + cr * bm;
@@ -663,26 +669,26 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
 
   // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
   if (is_neg(lm)) {
-    R sg = -lm * dtdx, h1 = R(0.5) * sg, h2 = R(1) - sg * two3;
+    R h1 = -lm * hdt, h2 = R(6) + lm * fdt;
     R ref[5];
 #pragma unroll
-    for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * a6[m]);
+    for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * c6[m]);
     R bp = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
     if (is_neg(lp)) {
-      sg = -lp * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
-      const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * a6[1]));
-      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      h1 = -lp * hdt; h2 = R(6) + lp * fdt;
+      const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * c6[1]));
+      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
       bp = rc * du + i2c2 * dp;
     }
     if (is_neg(u)) {
-      sg = -u * dtdx; h1 = R(0.5) * sg; h2 = R(1) - sg * two3;
-      const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * a6[0]));
-      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * a6[4]));
+      h1 = -u * hdt; h2 = R(6) + u * fdt;
+      const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * c6[0]));
+      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
       b0 = dr - ic2 * dp;
-      out[2] = aL[2] + h1 * (dA[2] + h2 * a6[2]);
-      out[3] = aL[3] + h1 * (dA[3] + h2 * a6[3]);
+      out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
+      out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
     }
     out[0] = ref[0] - (b0 + bp);
     out[1] = ref[1] - cr * bp;
@@ -770,7 +776,7 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const R wt = wgl * wl + wgr * wr;
   // Roe enthalpy: sum of w_K (E_K + p_K) / rho_K = sum of (E_K + p_K) / sqrt(rho_K), times iw
   const R Ht = ((El + pl) * rsl + (Er + pr) * rsr) * iw;
-  const R ct2 = gm1 * (Ht - R(0.5) * (ut * ut + vt * vt + wt * wt));
+  const R ct2 = gm1 * (Ht - half_of(ut * ut + vt * vt + wt * wt));
   R SL, SR;
   if (is_pos(ct2)) {
     const R ct = nr_sqrt(ct2);
@@ -911,7 +917,7 @@ __device__ __forceinline__ void conserved_of(const R* q, R igm1, R* u) {
   u[0] = q[0] * q[1];
   u[1] = q[0] * q[2];
   u[2] = q[0] * q[3];
-  u[3] = q[4] * igm1 + R(0.5) * q[0] * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  u[3] = q[4] * igm1 + half_of(q[0]) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
 template <typename R, int D>
@@ -1005,7 +1011,7 @@ __device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], con
     const R r = Consts<R>::SHARE_RSQRT ? nr_rsqrt(U[0]) : R(0);
     const R ir = Consts<R>::SHARE_RSQRT ? r * r : nr_rcp(U[0]);
     const R uu = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    const R kin = R(0.5) * (U[1] * uu + U[2] * v + U[3] * w);
+    const R kin = half_of(U[1] * uu + U[2] * v + U[3] * w);
     const R p = (gamma - R(1)) * (U[4] - kin);
     if (is_pos(p)) {
       q[0] = U[0];
