@@ -74,6 +74,11 @@ struct Consts<double> {
   // needs (saves FP64 instructions; in FP32 the extra live register costs
   // more occupancy than the reciprocal it saves)
   static constexpr bool SHARE_RSQRT = true;
+  // FP64 instructions are the scarce resource: an instruction that a warp
+  // issues with only some lanes active costs as much as a full one, so the
+  // limiter selects operands instead of branching, and the tracing skips a
+  // wave's block only when no lane of the warp needs it
+  static constexpr bool FP_BOUND = true;
   static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
   static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
   static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
@@ -82,6 +87,7 @@ template <>
 struct Consts<float> {
   static constexpr bool STORE_CONSERVED = false;
   static constexpr bool SHARE_RSQRT = false;
+  static constexpr bool FP_BOUND = false;
   static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
   static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
   static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
@@ -90,6 +96,15 @@ struct Consts<float> {
 template <typename R>
 __device__ __forceinline__ R* fields(unsigned char* work, const DevBox& b) {
   return reinterpret_cast<R*>(work + b.work_off);
+}
+
+// Whether c holds on any active lane of the warp (FP_BOUND types; else c
+// itself): a block guarded by it is skipped when no lane needs it, also where
+// the compiler predicates the block rather than branching around it.
+template <typename R>
+__device__ __forceinline__ bool any_in_warp(bool c) {
+  if constexpr (Consts<R>::FP_BOUND) return __any_sync(__activemask(), c);
+  return c;
 }
 
 __device__ __forceinline__ long long zone(const DevBox& b, int i, int j, int k) {
@@ -518,7 +533,7 @@ __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f,
   } else if (!dgt(ie_mul(R(2), fabs(dR)), fabs(dL))) {
     L = a0 - R(2) * dR;
   }
-  if (is_pos(f)) {
+  if (any_in_warp<R>(is_pos(f)) && is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
     Rt = f * a0 + (R(1) - f) * Rt;
   }
@@ -572,7 +587,14 @@ __device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
 template <typename R>
 __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   const R x = a0 - L, y = Rt - a0;
-  if (!same_sign(y, x)) {
+  if constexpr (Consts<R>::FP_BOUND) {
+    // one multiply-add, a0 - 2y or a0 + 2x, for whichever edge is replaced
+    const bool ss = same_sign(y, x);
+    const bool cl = ss && abs_gt_twice(x, y), cr = ss && !cl && abs_gt_twice(y, x);
+    const R t = fma(cl ? R(-2) : R(2), cl ? y : x, a0);
+    L = ss ? (cl ? t : L) : a0;
+    Rt = ss ? (cr ? t : Rt) : a0;
+  } else if (!same_sign(y, x)) {
     L = a0;
     Rt = a0;
   } else if (abs_gt_twice(x, y)) {
@@ -580,7 +602,7 @@ __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   } else if (abs_gt_twice(y, x)) {
     Rt = a0 + R(2) * x;
   }
-  if (is_pos(f)) {
+  if (any_in_warp<R>(is_pos(f)) && is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
     Rt = f * a0 + (R(1) - f) * Rt;
   }
@@ -642,19 +664,22 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
     R bm = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
-    if (is_pos(lm)) {
+    const bool wm = is_pos(lm), w0 = is_pos(u);
+    if (any_in_warp<R>(wm)) {
       h1 = lm * hdt; h2 = R(6) - lm * fdt;
       const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * c6[1]));
       const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
-      bm = -rc * du + i2c2 * dp;
+      if (wm) bm = -rc * du + i2c2 * dp;
     }
-    if (is_pos(u)) {
+    if (any_in_warp<R>(w0)) {
       h1 = u * hdt; h2 = R(6) - u * fdt;
       const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * c6[0]));
       const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
-      b0 = dr - ic2 * dp;
-      out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
-      out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
+      if (w0) {
+        b0 = dr - ic2 * dp;
+        out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
+        out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
+      }
     }
     out[0] = ref[0] - (bm + b0);
     out[1] = ref[1] + cr * bm;
@@ -676,19 +701,22 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
     R bp = R(0), b0 = R(0);
     out[2] = ref[2];
     out[3] = ref[3];
-    if (is_neg(lp)) {
+    const bool wp = is_neg(lp), w0 = is_neg(u);
+    if (any_in_warp<R>(wp)) {
       h1 = -lp * hdt; h2 = R(6) + lp * fdt;
       const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * c6[1]));
       const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
-      bp = rc * du + i2c2 * dp;
+      if (wp) bp = rc * du + i2c2 * dp;
     }
-    if (is_neg(u)) {
+    if (any_in_warp<R>(w0)) {
       h1 = -u * hdt; h2 = R(6) + u * fdt;
       const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * c6[0]));
       const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
-      b0 = dr - ic2 * dp;
-      out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
-      out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
+      if (w0) {
+        b0 = dr - ic2 * dp;
+        out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
+        out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
+      }
     }
     out[0] = ref[0] - (b0 + bp);
     out[1] = ref[1] - cr * bp;
@@ -751,11 +779,13 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // El, Er -> normal-frame flux.
 // Toro, Spruce & Speares 1994 with Roe-averaged bounds (Batten et al. 1997),
 // Davis bounds when the Roe sound speed is not real.  Only the star state on
-// the side of the contact that contains x/t = 0 is formed.  All square roots
-// and reciprocals come from two reciprocal square roots per side (sqrt(rho)
-// and 1/rho, c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed)
-// and three reciprocals; wave-speed min/max and sign tests run on the integer
-// pipe in FP64.
+// the side of the contact that contains x/t = 0 is formed, as the change
+// S_K (U*_K - U_K) of that side's flux written without 1/rho_K.  All square
+// roots and reciprocals come from two reciprocal square roots per side
+// (1/sqrt(rho), which gives sqrt(rho), and 1/sqrt(gamma p), which gives
+// c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed) and three
+// reciprocals; wave-speed min/max and sign tests run on the integer pipe in
+// FP64.
 template <typename R>
 __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R* F) {
   const R gm1 = gamma - R(1);
@@ -770,10 +800,10 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const R gpl = gamma * pl, gpr = gamma * pr;
   const R cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
   const R iw = nr_rcp(sl + sr);
-  const R wgl = sl * iw, wgr = sr * iw;
-  const R ut = wgl * ul + wgr * ur;
-  const R vt = wgl * vl + wgr * vr;
-  const R wt = wgl * wl + wgr * wr;
+  const R wgr = sr * iw;  // Roe weight of the right state; the left one is 1 - wgr
+  const R ut = ul + wgr * (ur - ul);
+  const R vt = vl + wgr * (vr - vl);
+  const R wt = wl + wgr * (wr - wl);
   // Roe enthalpy: sum of w_K (E_K + p_K) / rho_K = sum of (E_K + p_K) / sqrt(rho_K), times iw
   const R Ht = ((El + pl) * rsl + (Er + pr) * rsr) * iw;
   const R ct2 = gm1 * (Ht - half_of(ut * ut + vt * vt + wt * wt));
@@ -790,22 +820,25 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const R Ss = (pr - pl + ml * ul - mr * ur) * nr_rcp(ml - mr);
   const bool left = is_nonneg(Ss);
   const R rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
-  const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR, mK = left ? ml : mr;
-  const R rsK = left ? rsl : rsr;
-  const R mu = rK * uK;
+  const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR;
+  const R mu = rK * uK, hK = EK + pK;
   F[0] = mu;
   F[1] = mu * uK + pK;
-  F[4] = (EK + pK) * uK;
+  F[4] = hK * uK;
   const bool supersonic = left ? is_nonneg(SL) : !is_pos(SR);
   if (!supersonic) {
-    // fac = mK / (SK - S*) and pK / mK from one reciprocal of mK (SK - S*)
-    const R den = SK - Ss;
-    const R r = nr_rcp(mK * den);
-    const R fac = mK * mK * r;
-    const R eK = EK * (rsK * rsK) + (Ss - uK) * (Ss + pK * den * r);
-    F[0] += SK * (fac - rK);
-    F[1] += SK * (fac * Ss - mu);
-    F[4] += SK * (fac * eK - EK);
+    // F += S_K (U*_K - U_K) with U*_K = rho_K phi (1, S*, v_K, w_K,
+    // E_K / rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))),
+    // phi = (S_K - u_K) / (S_K - S*) = 1 + g, g = (S* - u_K) / (S_K - S*):
+    // U*_K - U_K = (rho_K g, rho_K (phi S* - u_K), ., .,
+    //               g (E_K + p_K) + rho_K phi S* (S* - u_K))
+    const R dsu = Ss - uK;
+    const R g = dsu * nr_rcp(SK - Ss);
+    const R phi = R(1) + g;
+    const R srk = SK * rK;
+    F[0] += srk * g;
+    F[1] += srk * (phi * Ss - uK);
+    F[4] += SK * (g * hK + rK * phi * Ss * dsu);
   }
   // the upwind side's star and outer states share its transverse velocity, so
   // the transverse momentum fluxes are the mass flux times that velocity
