@@ -105,26 +105,29 @@ __device__ __forceinline__ bool abs_gt_twice(R x, R y) { return fabs(x) > R(2) *
 // patterns were measured to cost FP64-pipe time on GB300, 32-bit ones run on
 // the integer pipe.  Same results as the generic forms (the ordering key
 // flips the magnitude bits of negative numbers; -0.0 orders below +0.0).
+// They combine their tests with bitwise operators and select rather than
+// branch: a data-dependent branch that splits a warp makes the FP64
+// instructions after it issue once per side until the warp reconverges.
 __device__ __forceinline__ bool hw_nz(int hi, unsigned lo) { return ((hi & 0x7fffffff) | (int)lo) != 0; }
 template <>
 __device__ __forceinline__ bool is_pos<double>(double x) {
   const int h = __double2hiint(x);
-  return h > 0 || (h == 0 && __double2loint(x) != 0);
+  return (h > 0) | ((h == 0) & (__double2loint(x) != 0));
 }
 template <>
 __device__ __forceinline__ bool is_neg<double>(double x) {
   const int h = __double2hiint(x);
-  return h < 0 && hw_nz(h, (unsigned)__double2loint(x));
+  return (h < 0) & hw_nz(h, (unsigned)__double2loint(x));
 }
 template <>
 __device__ __forceinline__ bool same_sign<double>(double x, double y) {
   const int hx = __double2hiint(x), hy = __double2hiint(y);
-  return (hx ^ hy) >= 0 && hw_nz(hx, (unsigned)__double2loint(x)) && hw_nz(hy, (unsigned)__double2loint(y));
+  return ((hx ^ hy) >= 0) & hw_nz(hx, (unsigned)__double2loint(x)) & hw_nz(hy, (unsigned)__double2loint(y));
 }
 template <>
 __device__ __forceinline__ bool opp_sign<double>(double x, double y) {
   const int hx = __double2hiint(x), hy = __double2hiint(y);
-  return (hx ^ hy) < 0 && hw_nz(hx, (unsigned)__double2loint(x)) && hw_nz(hy, (unsigned)__double2loint(y));
+  return ((hx ^ hy) < 0) & hw_nz(hx, (unsigned)__double2loint(x)) & hw_nz(hy, (unsigned)__double2loint(y));
 }
 template <>
 __device__ __forceinline__ bool dgt<double>(double a, double b) {
@@ -132,7 +135,7 @@ __device__ __forceinline__ bool dgt<double>(double a, double b) {
   const int sa = ha >> 31, sb = hb >> 31;  // all ones for negative numbers
   const int ka = ha ^ (sa & 0x7fffffff), kb = hb ^ (sb & 0x7fffffff);
   const unsigned ja = (unsigned)__double2loint(a) ^ (unsigned)sa, jb = (unsigned)__double2loint(b) ^ (unsigned)sb;
-  return ka > kb || (ka == kb && ja > jb);
+  return (ka > kb) | ((ka == kb) & (ja > jb));
 }
 template <>
 __device__ __forceinline__ double dmin<double>(double a, double b) { return dgt(a, b) ? b : a; }
@@ -149,12 +152,12 @@ __device__ __forceinline__ double half_of<double>(double x) {
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned mh = (unsigned)hi & 0x7fffffffu;
   constexpr unsigned E2 = 2u << 20, INF = 0x7ff00000u;
-  if (mh - E2 < INF - E2) return __hiloint2double(hi - (1 << 20), (int)lo);
-  if (mh >= INF) return x;
+  const bool dec = mh - E2 < INF - E2, keep = mh >= INF;
   const unsigned ql = (lo >> 1) | (mh << 31), qh = mh >> 1;
   const unsigned rl = ql + (lo & ql & 1u);  // a dropped half rounds an odd result up
-  const unsigned rh = qh + (rl < ql ? 1u : 0u);
-  return __hiloint2double((int)(rh | ((unsigned)hi & 0x80000000u)), (int)rl);
+  const unsigned rh = (qh + (rl < ql ? 1u : 0u)) | ((unsigned)hi & 0x80000000u);
+  const unsigned oh = dec ? (unsigned)hi - (1u << 20) : keep ? (unsigned)hi : rh;
+  return __hiloint2double((int)oh, (int)(dec | keep ? lo : rl));
 }
 // |x| > 2 |y| for finite x, y, on the magnitude bits: 2|y| is an exponent
 // increment of a normal |y| and the magnitude pattern doubled for a
@@ -164,16 +167,10 @@ template <>
 __device__ __forceinline__ bool abs_gt_twice<double>(double x, double y) {
   const unsigned hx = (unsigned)__double2hiint(x) & 0x7fffffffu, lx = (unsigned)__double2loint(x);
   const unsigned hy = (unsigned)__double2hiint(y) & 0x7fffffffu, ly = (unsigned)__double2loint(y);
-  unsigned h2, l2;
-  if (hy >= (1u << 20)) {
-    if (hy >= 0x7fe00000u) return false;
-    h2 = hy + (1u << 20);
-    l2 = ly;
-  } else {
-    h2 = (hy << 1) | (ly >> 31);
-    l2 = ly << 1;
-  }
-  return hx > h2 || (hx == h2 && lx > l2);
+  const bool nrm = hy >= (1u << 20);
+  const unsigned h2 = nrm ? hy + (1u << 20) : (hy << 1) | (ly >> 31);
+  const unsigned l2 = nrm ? ly : ly << 1;
+  return (hy < 0x7fe00000u) & ((hx > h2) | ((hx == h2) & (lx > l2)));
 }
 
 // FP32 keeps its comparisons and min/max native: the FP32 units are not the

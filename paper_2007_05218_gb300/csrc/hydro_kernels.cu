@@ -511,7 +511,7 @@ __device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W
 // with single IEEE operations, as for cs_interface; the edge values the
 // branches then produce feed only continuous stages and take the fast path
 // (approximate reciprocal, fused multiply-adds).
-template <typename R>
+template <typename R, bool BLEND = true>
 __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt) {
   const R dL = ie_sub(L, a0), dR = ie_sub(Rt, a0);
   if (!same_sign(dR, ie_sub(a0, L)) || !same_sign(ie_sub(ap, a0), ie_sub(a0, am))) {
@@ -533,7 +533,7 @@ __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f,
   } else if (!dgt(ie_mul(R(2), fabs(dR)), fabs(dL))) {
     L = a0 - R(2) * dR;
   }
-  if (any_in_warp<R>(is_pos(f)) && is_pos(f)) {
+  if (BLEND && is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
     Rt = f * a0 + (R(1) - f) * Rt;
   }
@@ -584,13 +584,13 @@ __device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
 // dA (a0 - (L + Rt)/2) > dA^2/6 and -dA^2/6 > dA (a0 - (L + Rt)/2), dA = x + y,
 // are |x| > 2|y| and |y| > 2|x|; each replaced edge equals the old one on the
 // boundary of its test, so the limiter is continuous there.
-template <typename R>
+template <typename R, bool BLEND = true>
 __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   const R x = a0 - L, y = Rt - a0;
   if constexpr (Consts<R>::FP_BOUND) {
     // one multiply-add, a0 - 2y or a0 + 2x, for whichever edge is replaced
     const bool ss = same_sign(y, x);
-    const bool cl = ss && abs_gt_twice(x, y), cr = ss && !cl && abs_gt_twice(y, x);
+    const bool cl = ss & abs_gt_twice(x, y), cr = ss & !cl & abs_gt_twice(y, x);
     const R t = fma(cl ? R(-2) : R(2), cl ? y : x, a0);
     L = ss ? (cl ? t : L) : a0;
     Rt = ss ? (cr ? t : Rt) : a0;
@@ -602,17 +602,17 @@ __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
   } else if (abs_gt_twice(y, x)) {
     Rt = a0 + R(2) * x;
   }
-  if (any_in_warp<R>(is_pos(f)) && is_pos(f)) {
+  if (BLEND && is_pos(f)) {
     L = f * a0 + (R(1) - f) * L;
     Rt = f * a0 + (R(1) - f) * Rt;
   }
 }
 
-template <typename R>
+template <typename R, bool BLEND = true>
 __device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1, R f, R& L, R& Rt) {
   L = ppm_face(am1, a0, dm1, d0);
   Rt = ppm_face(a0, ap1, d0, dp1);
-  cw84_limit(a0, f, L, Rt);
+  cw84_limit<R, BLEND>(a0, f, L, Rt);
 }
 
 // Conserved momenta (normal frame) and total energy of a traced edge state,
@@ -730,12 +730,11 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
   sink(0, out);
 }
 
-template <typename R, int D, int LIM>
-__device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
-  const long long vs = b.vs, s = b.s[D];
-  const R igm1 = Consts<R>::igm1(b);
-  const R f = W[FLD_CHI * vs + Z];
-  R a0[5], aL[5], aR[5];
+// The limited parabolas (edges aL, aR) of the five normal-frame variables
+// of zone Z along D, flattened by f when BLEND.
+template <typename R, int D, int LIM, bool BLEND>
+__device__ __forceinline__ void zone_parabolas(const R* __restrict__ W, long long vs, long long s, long long Z, R f,
+                                               R* a0, R* aL, R* aR) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const R* a = W + comp<D>(m) * vs + Z;
@@ -744,11 +743,26 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
     if constexpr (LIM == HYDRO_LIMITER_CS08) {
       aL[m] = dq[0];
       aR[m] = dq[s];
-      cs_parabola(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
+      cs_parabola<R, BLEND>(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
     } else {
-      parabola(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
+      parabola<R, BLEND>(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
     }
   }
+}
+
+template <typename R, int D, int LIM>
+__device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
+  const long long vs = b.vs, s = b.s[D];
+  const R igm1 = Consts<R>::igm1(b);
+  const R f = W[FLD_CHI * vs + Z];
+  R a0[5], aL[5], aR[5];
+  // FP64: a warp none of whose zones is flattened takes the copy without the
+  // flattening blend (the compiler predicates a blend guarded per zone, which
+  // then issues in every zone)
+  if (Consts<R>::FP_BOUND && !any_in_warp<R>(is_pos(f)))
+    zone_parabolas<R, D, LIM, false>(W, vs, s, Z, f, a0, aL, aR);
+  else
+    zone_parabolas<R, D, LIM, true>(W, vs, s, Z, f, a0, aL, aR);
   const R cs = W[FLD_C * vs + Z];
   trace_edges(a0, aL, aR, cs, dtdx, [&](int side, const R* out) {
 #pragma unroll
