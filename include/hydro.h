@@ -146,7 +146,7 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 /* Diagnostics: where the per-zone intermediates of box `box` live inside the
  * scratch buffer, for stage-by-stage checks.  *offset_bytes receives the byte
  * offset of the box's first field from the start of scratch_dev, *nfields the
- * number of fields (136) and *elem_bytes their element size (8 for
+ * number of fields (138) and *elem_bytes their element size (8 for
  * HYDRO_FP64, 4 for HYDRO_MIXED boxes).  Each field is a ghosted-box grid with
  * the state's pitch, plane and var_stride (in elements; fields are var_stride
  * elements apart), in this order: primitive q[5] = (rho,u,v,w,p); sound speed
@@ -156,8 +156,9 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
  * fluxes f1[6][5] for the ordered axis pairs xy,xz,yx,yz,zx,zy; final fluxes
  * f[3][5]; limited slopes dq[3][5] of the normal-frame variables of each axis;
  * conserved momenta (normal frame) and total energy of the left- and right-edge
- * states, um[3][4] and up[3][4] (HYDRO_FP64 boxes only: HYDRO_MIXED boxes
- * rebuild them from the primitive edge states where they are needed).
+ * states, um[3][4] and up[3][4], then 1/c and c/rho of each zone (these ten
+ * for HYDRO_FP64 boxes only: HYDRO_MIXED boxes form them where they are
+ * needed).
  * Fluxes are conserved-variable components; the flux through the low face of
  * zone (i,j,k) along d is stored at (i,j,k).  Values are defined only where
  * the step computes them (see also hydro_fuse_lines and hydro_set_method for

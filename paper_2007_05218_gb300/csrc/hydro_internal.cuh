@@ -28,7 +28,8 @@ constexpr double FLAT_OMEGA2 = 10.0;
 //   pairs (d,e) = xy,xz,yx,yz,zx,zy, f[d][5] final fluxes (conserved x,y,z order),
 //   dq[d][5] limited slopes of the normal-frame variables of axis d,
 //   um[d][4] / up[d][4] conserved momenta (normal frame) and total energy of
-//   the left-/right-edge states.
+//   the left-/right-edge states,
+//   ic = 1/c and cr = c/rho of each zone (FP64 boxes; for the tracing).
 // Flux of a d-face between zones Z-s_d and Z is stored at zone Z.
 enum Field : int {
   FLD_Q = 0,
@@ -42,7 +43,9 @@ enum Field : int {
   FLD_DQ = 97,
   FLD_UM = 112,
   FLD_UP = 124,
-  NFIELDS = 136
+  FLD_IC = 136,
+  FLD_CR = 137,
+  NFIELDS = 138
 };
 
 // Per-box geometry as the kernels see it (lives in the head of scratch).

@@ -79,6 +79,9 @@ struct Consts<double> {
   // limiter selects operands instead of branching, and the tracing skips a
   // wave's block only when no lane of the warp needs it
   static constexpr bool FP_BOUND = true;
+  // the primitive conversion stores 1/c and c/rho for the tracing, which
+  // reads them for each of the three axes instead of forming two reciprocals
+  static constexpr bool PRIM_RECIPROCALS = true;
   static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
   static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
   static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
@@ -88,6 +91,7 @@ struct Consts<float> {
   static constexpr bool STORE_CONSERVED = false;
   static constexpr bool SHARE_RSQRT = false;
   static constexpr bool FP_BOUND = false;
+  static constexpr bool PRIM_RECIPROCALS = false;
   static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
   static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
   static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
     const double* U = state + b.state_off;
     double rho = U[Z];
     if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
-    double u, v, w, p, cs;
+    double u, v, w, p, cs, ir = 0.0, ic = 0.0;
     if constexpr (EXACT) {
       u = __ddiv_rn(U[vs + Z], rho);
       v = __ddiv_rn(U[2 * vs + Z], rho);
@@ -247,13 +251,15 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
       cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(b.gamma, p), rho));
     } else {
-      const double ir = nr_rcp(rho);
+      ir = nr_rcp(rho);
       u = U[vs + Z] * ir;
       v = U[2 * vs + Z] * ir;
       w = U[3 * vs + Z] * ir;
       p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
       if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
-      cs = nr_sqrt(b.gamma * p * ir);
+      const double c2 = b.gamma * p * ir;
+      ic = nr_rsqrt(c2);
+      cs = c2 * ic;
     }
     if (b.precision == HYDRO_FP64) {
       double* W = fields<double>(work, b);
@@ -263,6 +269,12 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       W[3 * vs + Z] = w;
       W[4 * vs + Z] = p;
       W[FLD_C * vs + Z] = cs;
+      if constexpr (EXACT) {
+        ic = nr_rcp(cs);
+        ir = nr_rcp(rho);
+      }
+      W[FLD_IC * vs + Z] = ic;
+      W[FLD_CR * vs + Z] = cs * ir;
     } else {
       float* W = fields<float>(work, b);
       W[Z] = (float)rho;
@@ -628,11 +640,13 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
 
 // Characteristic tracing of one zone along one axis (Miller & Colella 2002
 // style, R4): zone values a0, limited parabola edges aL, aR of the five
-// normal-frame variables, zone sound speed cs, dt/dx.  Hands the right-edge
-// state (side 1, the left state of the zone's high face) and then the
-// left-edge state (side 0) to sink(side, q[5]) as soon as each is formed.
+// normal-frame variables, zone sound speed cs with ic = 1/c and cr = c/rho,
+// dt/dx.  Hands the right-edge state (side 1, the left state of the zone's
+// high face) and then the left-edge state (side 0) to sink(side, q[5]) as
+// soon as each is formed.
 template <typename R, typename Sink>
-__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R dtdx, Sink&& sink) {
+__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R ic, R cr, R dtdx,
+                                            Sink&& sink) {
   // The parabola's dA = aR - aL and a6 = 6 (a0 - (aL + aR)/2) (CW84 §1); the
   // factor 6 of a6 is carried by h2 below, so c6 holds a6 / 6.  For a wave
   // of speed lambda, sigma = |lambda| dt/dx, the average of the parabola over
@@ -645,11 +659,9 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
     c6[m] = a0[m] - half_of(aL[m] + aR[m]);
   }
   const R rho = a0[0], u = a0[1];
-  const R ic = nr_rcp(cs);
   const R rc = rho * half_of(ic);   // rho / 2c
   const R ic2 = ic * ic;            // 1 / c^2
   const R i2c2 = half_of(ic2);      // 1 / 2c^2
-  const R cr = cs * nr_rcp(rho);    // c / rho
   const R c2 = cs * cs;
   const R lm = u - cs, lp = u + cs;
   const R hdt = half_of(dtdx), fdt = R(4) * dtdx;
@@ -730,6 +742,12 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
   sink(0, out);
 }
 
+// The same with 1/c and c/rho formed here.
+template <typename R, typename Sink>
+__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R dtdx, Sink&& sink) {
+  trace_edges(a0, aL, aR, cs, nr_rcp(cs), cs * nr_rcp(a0[0]), dtdx, sink);
+}
+
 // The limited parabolas (edges aL, aR) of the five normal-frame variables
 // of zone Z along D, flattened by f when BLEND.
 template <typename R, int D, int LIM, bool BLEND>
@@ -764,11 +782,15 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
   else
     zone_parabolas<R, D, LIM, true>(W, vs, s, Z, f, a0, aL, aR);
   const R cs = W[FLD_C * vs + Z];
-  trace_edges(a0, aL, aR, cs, dtdx, [&](int side, const R* out) {
+  auto sink = [&](int side, const R* out) {
 #pragma unroll
     for (int m = 0; m < 5; m++) W[((side ? FLD_QP : FLD_QM) + 5 * D + m) * vs + Z] = out[m];
     if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, side ? FLD_UP : FLD_UM, out, igm1);
-  });
+  };
+  if constexpr (Consts<R>::PRIM_RECIPROCALS)
+    trace_edges(a0, aL, aR, cs, W[FLD_IC * vs + Z], W[FLD_CR * vs + Z], dtdx, sink);
+  else
+    trace_edges(a0, aL, aR, cs, dtdx, sink);
 }
 
 template <typename R, int LIM>

@@ -1,0 +1,134 @@
+// Checks the device arithmetic helpers of fp64_fast.cuh on the GPU against
+// IEEE operations: the bit-pattern sign tests, comparisons, min/max, exact
+// halving and the |x| > 2|y| test bit for bit, on patterns drawn over every
+// exponent (subnormals, the range edges, zero and both signs included); the
+// Newton-refined reciprocal, reciprocal square root and square root within
+// their stated error over normal arguments.  Prints one line per check and
+// exits non-zero on any mismatch.  Built and run by test_gpu_fp64_helpers.py.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "fp64_fast.cuh"
+
+using namespace hydro;
+
+enum { BAD_HALF, BAD_CMP, BAD_RCP, BAD_SQRT, BAD_RSQRT, NBAD };
+
+__device__ double ulp_of(double r) { return ldexp(1.0, ilogb(r) - 52); }
+
+__global__ void check_bits(const double* x, const double* y, int n, unsigned long long* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = x[i], c = y[i];
+  const double h = half_of<double>(a), r = __dmul_rn(0.5, a);
+  if (!(__double_as_longlong(h) == __double_as_longlong(r) || (isnan(h) && isnan(r)))) atomicAdd(&bad[BAD_HALF], 1ull);
+  if (!isfinite(a) || !isfinite(c)) return;
+  bool e = abs_gt_twice<double>(a, c) != (fabs(a) > __dmul_rn(2.0, fabs(c)));
+  e |= is_pos<double>(a) != (a > 0.0);
+  e |= is_neg<double>(a) != (a < 0.0);
+  e |= same_sign<double>(a, c) != ((a > 0.0 && c > 0.0) || (a < 0.0 && c < 0.0));
+  e |= opp_sign<double>(a, c) != ((a > 0.0 && c < 0.0) || (a < 0.0 && c > 0.0));
+  if (!(a == 0.0 && c == 0.0)) {  // the bit-pattern order puts -0.0 below +0.0
+    e |= dgt<double>(a, c) != (a > c);
+    e |= dmin<double>(a, c) != fmin(a, c);
+    e |= dmax<double>(a, c) != fmax(a, c);
+  }
+  if (e) atomicAdd(&bad[BAD_CMP], 1ull);
+}
+
+// x > 0 normal: reciprocal and square root within 2 ulp of the correctly
+// rounded results; 1/sqrt(x) within 2^-51.5 relative, from the residual
+// y^2 x - 1 formed with an exact square.  The largest errors in units of 1e-3
+// ulp (resp. of 2^-53) are kept in worst[].
+__global__ void check_refined(const double* x, int n, unsigned long long* bad, unsigned long long* worst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = x[i];
+  const double rr = __drcp_rn(a), er = fabs(nr_rcp(a) - rr) / ulp_of(rr);
+  const double sr = __dsqrt_rn(a), es = fabs(nr_sqrt(a) - sr) / ulp_of(sr);
+  const double y = nr_rsqrt(a);
+  const double t = y * y, tl = fma(y, y, -t);
+  const double res = fma(a, t, -1.0) + a * tl;  // y^2 a - 1
+  const double eq = fabs(0.5 * res) * 9007199254740992.0;  // relative error of y in units of 2^-53
+  if (!(er <= 2.0)) atomicAdd(&bad[BAD_RCP], 1ull);
+  if (!(es <= 2.0)) atomicAdd(&bad[BAD_SQRT], 1ull);
+  if (!(eq <= 2.83)) atomicAdd(&bad[BAD_RSQRT], 1ull);
+  atomicMax(&worst[0], (unsigned long long)(er * 1000.0));
+  atomicMax(&worst[1], (unsigned long long)(es * 1000.0));
+  atomicMax(&worst[2], (unsigned long long)(eq * 1000.0));
+}
+
+static double from_pattern(uint64_t b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+
+int main() {
+  std::mt19937_64 g(20070521);
+  std::vector<double> x, y;
+  const uint64_t edges[] = {0, 1, 2, 3, 5, 0x000fffffffffffffull, 0x000ffffffffffffeull, 0x0010000000000000ull,
+                            0x0010000000000001ull, 0x001fffffffffffffull, 0x0020000000000000ull,
+                            0x0020000000000001ull, 0x3ff0000000000000ull, 0x7fdfffffffffffffull,
+                            0x7fe0000000000000ull, 0x7fefffffffffffffull, 0x7ff0000000000000ull,
+                            0x7ff8000000000000ull, 0x0000000100000000ull, 0x00000000ffffffffull,
+                            0x0000000080000001ull, 0x0000000180000000ull};
+  for (uint64_t p : edges)
+    for (uint64_t q : edges)
+      for (uint64_t sp : {0ull, 1ull << 63})
+        for (uint64_t sq : {0ull, 1ull << 63}) {
+          x.push_back(from_pattern(p | sp));
+          y.push_back(from_pattern(q | sq));
+        }
+  for (int i = 0; i < (1 << 22); i++) {
+    uint64_t p = g(), q = g();
+    const uint64_t ep = g() % 2048;
+    uint64_t eq = (i % 4 == 0) ? g() % 8 : (i % 4 == 1) ? (ep ? ep - 1 : 0) : g() % 2048;  // tiny y; |x| near 2|y|
+    p = (p & 0x800fffffffffffffull) | (ep << 52);
+    q = (q & 0x800fffffffffffffull) | (eq << 52);
+    if (i % 8 == 3) q = (q & 0xfff0000000000000ull) | (p & 0x000fffffffffffffull);  // |x| == 2|y| exactly
+    if (i % 16 == 5) p = (p & 0x8000000000000000ull) | (g() % 0x0020000000000000ull);  // subnormal or smallest normal x
+    x.push_back(from_pattern(p));
+    y.push_back(from_pattern(q));
+  }
+  // normal positive arguments for the refined operations, 2^-1000 .. 2^1000
+  std::vector<double> z(1 << 22);
+  for (double& v : z) v = from_pattern(((uint64_t)(23 + g() % 2001) << 52) | (g() & 0x000fffffffffffffull));
+
+  const int n = (int)x.size(), nz = (int)z.size();
+  double *dx, *dy, *dz;
+  unsigned long long *dbad, *dworst;
+  cudaMalloc(&dx, n * sizeof(double));
+  cudaMalloc(&dy, n * sizeof(double));
+  cudaMalloc(&dz, nz * sizeof(double));
+  cudaMalloc(&dbad, NBAD * sizeof(unsigned long long));
+  cudaMalloc(&dworst, 3 * sizeof(unsigned long long));
+  cudaMemcpy(dx, x.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(dy, y.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(dz, z.data(), nz * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemset(dbad, 0, NBAD * sizeof(unsigned long long));
+  cudaMemset(dworst, 0, 3 * sizeof(unsigned long long));
+  check_bits<<<(n + 255) / 256, 256>>>(dx, dy, n, dbad);
+  check_refined<<<(nz + 255) / 256, 256>>>(dz, nz, dbad, dworst);
+  const cudaError_t err = cudaDeviceSynchronize();
+  unsigned long long bad[NBAD] = {}, worst[3] = {};
+  cudaMemcpy(bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost);
+  cudaMemcpy(worst, dworst, sizeof(worst), cudaMemcpyDeviceToHost);
+  std::printf("cuda %s\n", cudaGetErrorString(err));
+  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu\n", n, bad[BAD_HALF],
+              bad[BAD_CMP]);
+  std::printf("refined cases %d: rcp > 2 ulp %llu (max %.3f), sqrt > 2 ulp %llu (max %.3f), rsqrt > 2^-51.5 %llu "
+              "(max %.3f x 2^-53)\n",
+              nz, bad[BAD_RCP], worst[0] / 1000.0, bad[BAD_SQRT], worst[1] / 1000.0, bad[BAD_RSQRT],
+              worst[2] / 1000.0);
+  bool ok = err == cudaSuccess;
+  for (unsigned long long b : bad) ok = ok && b == 0;
+  std::printf("%s\n", ok ? "PASS" : "FAIL");
+  return ok ? 0 : 1;
+}

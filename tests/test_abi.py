@@ -62,7 +62,7 @@ def test_workspace_and_layout_planning():
     assert lay.var_stride >= lay.plane * 17 and lay.var_stride % 32 == 0
     assert sb == 5 * lay.var_stride * 8
     off, nf, eb = hydro.hydro_debug_fields([d], 0)
-    assert nf == 136 and eb == 8 and off % 256 == 0
+    assert nf == 138 and eb == 8 and off % 256 == 0
     assert wb >= off + nf * lay.var_stride * 8
     # a mixed-precision box keeps FP32 fields: half the scratch bytes
     dm = hydro.desc_of(pr, hydro.HYDRO_MIXED)

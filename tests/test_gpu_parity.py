@@ -124,10 +124,16 @@ def test_every_stage_matches_oracle_on_one_step(name):
     B.step(1, dt=torch.tensor([dt], dtype=torch.float64, device="cuda"))
     B.sync()
     Wg = B.field_view(0, 0, oracle.W_NFIELDS).cpu().numpy()
+    nf = hydro.hydro_debug_fields(B.descs, 0)[1]
+    recips = B.field_view(0, nf - 2, 2).cpu().numpy()  # 1/c and c/rho of each zone (FP64 boxes)
     Ugpu = B.interior(0)
     B.close()
     bad = []
     regions = _regions(pr.shape)
+    reg = regions[oracle.W_C][1]
+    c, rho = W[oracle.W_C][reg], W[0][reg]
+    assert np.max(np.abs(recips[0][reg] * c - 1.0)) <= 1e-13
+    assert np.max(np.abs(recips[1][reg] * rho / c - 1.0)) <= 1e-13
     for f, (label, reg) in regions.items():
         a, b = Wg[f][reg], W[f][reg]
         # scale: the largest magnitude among the five fields of the same group
