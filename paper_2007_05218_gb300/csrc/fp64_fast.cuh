@@ -8,9 +8,12 @@
 //   1/x:       e = 1 - x y,    y <- y (1 + e + e^2)
 //   1/sqrt(x): e = 1 - x y^2,  y <- y (1 + e/2 + 3 e^2 / 8)
 // A seed with relative error eps (about 2^-20 here) leaves O(eps^3) plus a few
-// roundings: within 1.2 ulp as measured on GB300, for 3 to 6 FP64-pipe
-// instructions instead of the ~10 pipe slots an IEEE divide or square root
-// takes.  Arguments must be non-zero normal numbers (positive for the square
+// roundings: measured on GB300 over normal arguments from 2^-1000 to 2^1000
+// (tests/fp64_helpers_check.cu), the reciprocal is within 1.0 ulp of the
+// correctly rounded one, the square root (x times its reciprocal square root)
+// within 1.7 ulp and the reciprocal square root within 1.25 x 2^-53 relative,
+// for 3 to 6 FP64-pipe instructions instead of the ~10 pipe slots an IEEE
+// divide or square root takes.  Arguments must be non-zero normal numbers (positive for the square
 // roots): the callers pass densities, pressures, sound-speed products and
 // wave-speed differences that the method keeps away from zero.
 //
