@@ -52,6 +52,21 @@ FLOPS_PER_UNIT = {
 TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.554852e9 + 0.519146e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.074 GB / 12.88 M faces
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest of the ranks' values of x (x itself on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world: int, dist=None, device="cuda") -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds, dist, device)
+
+
 def units_per_launch(stage: str, n) -> int:
     """Units of work one launch of `stage` processes on a box of n = (nx, ny, nz)."""
     nx, ny, nz = n
@@ -374,12 +389,8 @@ def main() -> None:
     prof = hydro.hydro_profile_end(B.h)
     launches = hydro.hydro_kernel_launches(B.h) - launches0
     B.sync()  # raises on a nonphysical state
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = t.item()
-    value = world * N * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(N * args.steps, ms_max * 1e-3, world)  # ms_max: the slowest rank's time already
 
     # ---- end to end through the C ABI: pinned host IC -> K steps -> host result
     nbytes = pr.U.nbytes
@@ -394,11 +405,7 @@ def main() -> None:
     hydro.hydro_download(B.h, host_out.numpy(), stream)
     e2e_s = time.perf_counter() - t0
     B.sync()
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e = {"value": world * N * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": whole_job_rate(N * args.steps, e2e_s, world, dist), "unit": UNIT,
            "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
            "what": "hydro_upload of the interior initial state from pinned host memory, K steps, "
                    "hydro_download of the final interior state (bytes per step = solve bytes / K)"}
@@ -434,7 +441,7 @@ def main() -> None:
     variants = None if args.no_variants else run_variants(hydro, torch, pr, stream, args.warmup)
     batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
     served = run_served(hydro, inputs, torch, np, args.served_requests) if args.served_requests > 0 else None
-    mixed = {"value": world * N * args.steps / (ms_mixed * 1e-3), "unit": UNIT,
+    mixed = {"value": whole_job_rate(N * args.steps, ms_mixed * 1e-3, world, dist), "unit": UNIT,
              "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
              "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
 
