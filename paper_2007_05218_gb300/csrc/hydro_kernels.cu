@@ -439,15 +439,62 @@ __device__ __forceinline__ double vl_slope<double>(double am, double a0, double 
   return __hiloint2double((int)(mh | ((unsigned)hc & 0x80000000u)), (int)ml);  // sign of ap - am
 }
 
+// The FP64 slope from its differences dl = a0 - am, dr = ap - a0 and
+// sum = ap - am when every exponent involved is in the range where the
+// halving and doublings are exponent changes: integer selections only, no
+// branch (0 for a zone that is not monotone).
+__device__ __forceinline__ double vl_slope_normal(double dl, double dr, double sum) {
+  const int hl = __double2hiint(dl), ll = __double2loint(dl);
+  const int hr = __double2hiint(dr), lr = __double2loint(dr);
+  const int hc = __double2hiint(sum), lc = __double2loint(sum);
+  const bool mono = ((hl ^ hr) >= 0) & hw_nonzero(hl, ll) & hw_nonzero(hr, lr);
+  constexpr int ONE_EXP = 1 << 20;
+  unsigned mh = (unsigned)((hc & 0x7fffffff) - ONE_EXP), ml = (unsigned)lc;
+  const unsigned h2 = (unsigned)((hl & 0x7fffffff) + ONE_EXP), l2 = (unsigned)ll;
+  const bool t2 = (h2 < mh) | ((h2 == mh) & (l2 < ml));
+  mh = t2 ? h2 : mh;
+  ml = t2 ? l2 : ml;
+  const unsigned h3 = (unsigned)((hr & 0x7fffffff) + ONE_EXP), l3 = (unsigned)lr;
+  const bool t3 = (h3 < mh) | ((h3 == mh) & (l3 < ml));
+  mh = t3 ? h3 : mh;
+  ml = t3 ? l3 : ml;
+  return __hiloint2double(mono ? (int)(mh | ((unsigned)hc & 0x80000000u)) : 0, mono ? (int)ml : 0);
+}
+
+// Whether a monotone zone's differences leave that exponent range.
+__device__ __forceinline__ bool vl_slope_odd(double dl, double dr, double sum) {
+  const int hl = __double2hiint(dl), hr = __double2hiint(dr), hc = __double2hiint(sum);
+  const bool mono = ((hl ^ hr) >= 0) & hw_nonzero(hl, __double2loint(dl)) & hw_nonzero(hr, __double2loint(dr));
+  const int ec = (hc >> 20) & 0x7ff, el = (hl >> 20) & 0x7ff, er = (hr >> 20) & 0x7ff;
+  return mono & ((ec < 2) | (el < 1) | (er < 1) | (el > 0x7fd) | (er > 0x7fd));
+}
+
 // Limited slopes of the five normal-frame variables of axis D, once per zone
-// of [-2, n_D+1] along D and [-1, n] across it.
+// of [-2, n_D+1] along D and [-1, n] across it.  FP64: per variable the three
+// differences first, then one warp-wide choice between the integer-only
+// selection and vl_slope (for a warp with a difference near the subnormal or
+// overflow range), so that no lane's early exit splits the warp.
 template <typename R, int D>
 __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, long long Z) {
   const long long vs = b.vs, s = b.s[D];
+  if constexpr (Consts<R>::FP_BOUND) {
 #pragma unroll
-  for (int m = 0; m < 5; m++) {
-    const R* a = W + comp<D>(m) * vs + Z;
-    W[(FLD_DQ + 5 * D + m) * vs + Z] = vl_slope(a[-s], a[0], a[s]);
+    for (int m = 0; m < 5; m++) {
+      const R* a = W + comp<D>(m) * vs + Z;
+      const R am = a[-s], a0 = a[0], ap = a[s];
+      const R dl = a0 - am, dr = ap - a0, sum = ap - am;
+      R* out = W + (FLD_DQ + 5 * D + m) * vs + Z;
+      if (any_in_warp<R>(vl_slope_odd(dl, dr, sum)))
+        *out = vl_slope(am, a0, ap);
+      else
+        *out = vl_slope_normal(dl, dr, sum);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      const R* a = W + comp<D>(m) * vs + Z;
+      W[(FLD_DQ + 5 * D + m) * vs + Z] = vl_slope(a[-s], a[0], a[s]);
+    }
   }
 }
 
@@ -841,7 +888,8 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const R vt = vl + wgr * (vr - vl);
   const R wt = wl + wgr * (wr - wl);
   // Roe enthalpy: sum of w_K (E_K + p_K) / rho_K = sum of (E_K + p_K) / sqrt(rho_K), times iw
-  const R Ht = ((El + pl) * rsl + (Er + pr) * rsr) * iw;
+  const R hl = El + pl, hr = Er + pr;
+  const R Ht = (hl * rsl + hr * rsr) * iw;
   const R ct2 = gm1 * (Ht - half_of(ut * ut + vt * vt + wt * wt));
   R SL, SR;
   if (is_pos(ct2)) {
@@ -857,7 +905,7 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
   const bool left = is_nonneg(Ss);
   const R rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
   const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR;
-  const R mu = rK * uK, hK = EK + pK;
+  const R mu = rK * uK, hK = left ? hl : hr;
   F[0] = mu;
   F[1] = mu * uK + pK;
   F[4] = hK * uK;
