@@ -49,7 +49,7 @@ FLOPS_PER_UNIT = {
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
 # stands; a stage missing here has no capture of its current code and reports
 # traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.554852e9 + 0.519146e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.074 GB / 12.88 M faces
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.554235e9 + 0.519544e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.074 GB / 12.88 M faces
 
 
 def max_over_ranks(x: float, dist=None, device="cuda") -> float:
