@@ -21,7 +21,8 @@
 // Stages (paper §3: limited slopes from neighbours, then a polynomial
 // reconstruction; the published methods are cited per stage):
 //   k_fill       ghost zones from the boundary conditions (x, then y, then z)
-//   k_prim       conserved -> primitive + EOS (FP64); per-box max signal speed
+//   k_prim       conserved -> primitive + EOS (FP64); per-box max signal speed;
+//                1/c and c/rho for the FP64 tracing
 //   k_dt         dt = cfl / max((|u_d|+c)/dx_d)
 //   k_flatten    CW84 §4 shock flattening coefficient (max over directions)
 //   k_slopes     CW84 limited slopes, once per zone and axis (none for CS08)
@@ -218,13 +219,14 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
 
 // ------------------------------------------------- conserved -> primitive, dt
 // FP64 arithmetic for every box (the dt reduction needs it); the primitive
-// fields are stored in the box's compute type.
+// fields are stored in the box's compute type, and for FP64 boxes also 1/c
+// and c/rho, which the tracing reads on each axis.
 // EXACT (used under the CS08 limiter, whose branches are not continuous in
 // their inputs): the primitive state with correctly rounded divides and square
 // root and no fused multiply-adds, u = U1 / rho, ..., p = (gamma - 1)(E -
 // (rho / 2)(u^2 + v^2 + w^2)), c = sqrt(gamma p / rho), in that order, so that
 // the limiter's decisions are reproducible on any IEEE machine.  Otherwise one
-// approximate reciprocal and square root.
+// refined reciprocal and one reciprocal square root (1/c; c = c^2 / c).
 template <bool EXACT>
 __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes,
                                               const double* __restrict__ state, unsigned char* __restrict__ work,
