@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
 // root and no fused multiply-adds, u = U1 / rho, ..., p = (gamma - 1)(E -
 // (rho / 2)(u^2 + v^2 + w^2)), c = sqrt(gamma p / rho), in that order, so that
 // the limiter's decisions are reproducible on any IEEE machine.  Otherwise one
-// refined reciprocal and one reciprocal square root (1/c; c = c^2 / c).
+// refined reciprocal (1/rho) and one refined reciprocal square root, of c^2,
+// which is 1/c and gives c = c^2 (1/c).
 template <bool EXACT>
 __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes,
                                               const double* __restrict__ state, unsigned char* __restrict__ work,
