@@ -52,6 +52,30 @@ FLOPS_PER_UNIT = {
 TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.554235e9 + 0.519544e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.074 GB / 12.88 M faces
 
 
+# Compulsory HBM traffic of one zone-update in every form: the FP64 state
+# (5 doubles per zone) read and written once per step.
+STATE_BYTES_PER_ZONE_UPDATE = 2 * 5 * 8
+
+
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth of these GPUs (GB/s) and where it comes from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, TypeError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def hbm_fraction(zone_updates_per_s: float) -> dict:
+    """A rate's compulsory state traffic as a fraction of the HBM roofline."""
+    peak, src = hbm_peak_gbs()
+    gbs = zone_updates_per_s * STATE_BYTES_PER_ZONE_UPDATE / 1e9
+    return {"bytes_per_zone_update": STATE_BYTES_PER_ZONE_UPDATE, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "peak_source": src,
+            "what": "compulsory traffic (the FP64 state read and written once per step) at the measured rate; "
+                    "the step is bound by the FP64 pipe (see roofline), so this is the HBM headroom"}
+
+
 def max_over_ranks(x: float, dist=None, device="cuda") -> float:
     """The largest of the ranks' values of x (x itself on one rank)."""
     if dist is None:
@@ -229,7 +253,8 @@ def run_batched(hydro, inputs, torch, np, stream, nboxes=512, nsteps=30):
         finals[name] = [B.interior(k)[[0, 4]] for k in range(nboxes)]
         B.close()
         del B
-        out[name] = {"value": zones * nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / nsteps,
+        rate = zones * nsteps / (ms * 1e-3)
+        out[name] = {"value": rate, "unit": UNIT, "ms_per_step": ms / nsteps, "hbm": hbm_fraction(rate),
                      "tuned": {f"{t[0]}{'' if t[1] == 0 else '_mixed'}": [t[2], t[3]] for t in tuned}}
     worst = {n: max(float(np.abs(finals["mixed"][k][i] - finals["fp64"][k][i]).sum()
                           / np.abs(finals["fp64"][k][i]).sum()) for k in range(nboxes))
@@ -312,7 +337,7 @@ def run_served(hydro, inputs, torch, np, nrequests, budget_gb=120.0, max_active=
     return {"workload": f"served_stream_{nrequests}", "requests": nrequests,
             "offered_rate_req_per_s": 200.0,
             "offered_zone_updates_per_s": work / span_arrivals if span_arrivals > 0 else None,
-            "value": work / makespan, "unit": UNIT, "makespan_s": makespan,
+            "value": work / makespan, "unit": UNIT, "hbm": hbm_fraction(work / makespan), "makespan_s": makespan,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_queued_s": float(np.mean(queued)), "budget_gb": budget_gb, "max_active": max_active,
             "peak_pool_gb": st["peak_bytes"] / 1e9, "ticks": st["ticks"],
@@ -441,7 +466,8 @@ def main() -> None:
     variants = None if args.no_variants else run_variants(hydro, torch, pr, stream, args.warmup)
     batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
     served = run_served(hydro, inputs, torch, np, args.served_requests) if args.served_requests > 0 else None
-    mixed = {"value": whole_job_rate(N * args.steps, ms_mixed * 1e-3, world, dist), "unit": UNIT,
+    mixed_rate = whole_job_rate(N * args.steps, ms_mixed * 1e-3, world, dist)
+    mixed = {"value": mixed_rate, "unit": UNIT, "hbm": hbm_fraction(mixed_rate),
              "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
              "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
 
@@ -463,6 +489,11 @@ def main() -> None:
                             if top in TRAFFIC_BYTES_PER_UNIT else None),
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "flops_per_launch": flops}
+    hbm = hbm_fraction(value)
+    if roofline["traffic"] is not None:
+        # the dominant kernel's DRAM bytes per launch (ncu) over its live launch time
+        gbs = roofline["traffic"] / avg_s / 1e9
+        hbm["dominant_kernel"] = {"kernel": f"k_{top}", "dram_gbs": gbs, "frac": gbs / hbm["peak_gbs"]}
     total_flops = sum(FLOPS_PER_UNIT[s] * units_per_launch(s, n) for s in FLOPS_PER_UNIT)
     step_fp64 = total_flops / (ms / args.steps * 1e-3)
 
@@ -482,6 +513,7 @@ def main() -> None:
                          % (B_state_gb, B_scratch_gb),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "hbm": hbm,
         "fp64_algorithmic_tflops_whole_step": step_fp64 / 1e12,
         "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "cpu_baseline": cpu,
