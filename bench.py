@@ -36,6 +36,11 @@ N_BOX = 256
 # FP64 peak for the ALU roofline: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz.
 # (GB300 nominal FP64 is 1.25 TFLOP/s; 1.25e12 / (152 x 2.07e9) = 4 flop/clk/SM.)
 FP64_PEAK_FLOPS = 152 * 4 * 2070e6
+# FP32 peak for the mixed form's FP32 stages: 152 SMs x 128 FP32 lanes x 2
+# flop (fused multiply-add) x 2070 MHz = 80.5 TFLOP/s, nominal.
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2070e6
+# The stages the mixed form computes in FP32 (the rest stay FP64).
+FP32_STAGES_MIXED = ("flatten", "slopes", "trace", "riemann", "ctu1", "ctu2")
 
 # Algorithmic FP64 flops (add/sub, mul, div, sqrt; each counts 1) per unit of
 # work of each stage, counted by the oracle (python -m oracle.count_flops
@@ -74,6 +79,22 @@ def hbm_fraction(zone_updates_per_s: float) -> dict:
             "frac": gbs / peak, "peak_source": src,
             "what": "compulsory traffic (the FP64 state read and written once per step) at the measured rate; "
                     "the step is bound by the FP64 pipe (see roofline), so this is the HBM headroom"}
+
+
+def fp32_pipe(n, step_ms: float, stage_ms: dict) -> dict:
+    """Algorithmic flops of the mixed form's FP32 stages (the oracle's counts,
+    which hold for either precision) per second, over the whole step and over
+    those stages' own time, against the FP32 peak."""
+    flops = sum(FLOPS_PER_UNIT[s] * units_per_launch(s, n) for s in FP32_STAGES_MIXED)
+    own_ms = sum(stage_ms.get(s, 0.0) for s in FP32_STAGES_MIXED)
+    whole = flops / (step_ms * 1e-3)
+    own = flops / (own_ms * 1e-3) if own_ms > 0 else None
+    return {"algorithmic_tflops_whole_step": whole / 1e12, "frac_whole_step": whole / FP32_PEAK_FLOPS,
+            "algorithmic_tflops_in_fp32_stages": None if own is None else own / 1e12,
+            "frac_in_fp32_stages": None if own is None else own / FP32_PEAK_FLOPS,
+            "peak_tflops": FP32_PEAK_FLOPS / 1e12,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (nominal)",
+            "stages": list(FP32_STAGES_MIXED)}
 
 
 def max_over_ranks(x: float, dist=None, device="cuda") -> float:
@@ -467,9 +488,11 @@ def main() -> None:
     batched = None if args.no_batched else run_batched(hydro, inputs, torch, np, stream)
     served = run_served(hydro, inputs, torch, np, args.served_requests) if args.served_requests > 0 else None
     mixed_rate = whole_job_rate(N * args.steps, ms_mixed * 1e-3, world, dist)
+    mixed_stage_ms = {k: v[1] / args.steps for k, v in prof_mixed.items()}
     mixed = {"value": mixed_rate, "unit": UNIT, "hbm": hbm_fraction(mixed_rate),
+             "fp32_pipe": fp32_pipe(n, ms_mixed / args.steps, mixed_stage_ms),
              "ms_per_step": ms_mixed / args.steps, "dtype": "f32 reconstruct/trace/Riemann, f64 state/update/dt",
-             "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof_mixed.items()}}
+             "rel_l1_vs_fp64": rel_l1, "stages_ms_per_step": mixed_stage_ms}
 
     if rank != 0:
         if dist is not None:
