@@ -138,7 +138,11 @@ def _one_step_fields(pr, fuse, riemann=0):
     hydro.hydro_fuse_lines(B.h, fuse)
     B.step(1, dt=torch.tensor([dt], dtype=torch.float64, device="cuda"))
     B.sync()
-    W = B.field_view(0, 0, oracle.W_NFIELDS).cpu().numpy().astype(np.float64)
+    # zones a field does not cover hold whatever the scratch held, signalling
+    # NaN patterns included, whose widening raises numpy's invalid flag; only
+    # the covered regions are compared
+    with np.errstate(invalid="ignore"):
+        W = B.field_view(0, 0, oracle.W_NFIELDS).cpu().numpy().astype(np.float64)
     U = B.interior(0)
     B.close()
     return W, U
