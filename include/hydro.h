@@ -275,23 +275,30 @@ int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, in
  * needs a handle, and a handle needs a caller-allocated scratch buffer of
  * about 136 doubles per ghosted zone; this call needs neither.
  *
- * Writes dt_dev[b] = cfl * min over interior zones and axes of dx/(|u|+c)
- * for boxes d[0..nboxes-1] whose states sit in state_dev with the layout
- * hydro_box_layout gives (the same result as hydro_compute_dt).  state_dev
- * (input) and dt_dev (output, nboxes doubles) are device pointers owned by the
- * caller.  Its scratch is a fixed static device array inside the library
- * (about 96 KB, held by every GPU that loads the library until the process
- * exits) with room for HYDRO_NOALLOC_MAX_BOXES boxes; a larger nboxes returns
- * HYDRO_ERR_INVALID with a message saying so.  The call allocates nothing.
+ * Writes dt_dev[b] = cfl / max over interior zones and axes a of
+ * (|u_a| + c) / dx_a (the CFL step, cfl * min of dx_a / (|u_a| + c), up to
+ * rounding) for boxes d[0..nboxes-1] whose states sit in state_dev with the
+ * layout hydro_box_layout gives.  The speeds are formed by the same device
+ * code as in hydro_compute_dt, so under the default limiter the two calls give
+ * the same time steps bit for bit (under HYDRO_LIMITER_CS08 a handle forms its
+ * primitive state with correctly rounded divides and the two agree to
+ * rounding).  state_dev (input) and dt_dev (output, nboxes doubles) are
+ * device pointers owned by the caller.  Its scratch is a fixed static device
+ * array inside the library (about 100 KB, held by every GPU that loads the
+ * library until the process exits) with room for HYDRO_NOALLOC_MAX_BOXES
+ * boxes; a larger nboxes returns HYDRO_ERR_INVALID with a message saying so.
+ * The call allocates nothing.
  *
  * The first call on a device looks up the device address of that array
- * (once per device, with the device current); make that first call before
- * any stream capture.  Every call on a device shares the one array: each call
- * rewrites the box table and clears the per-box maxima before its kernels
- * run, so calls ordered on one stream are safe, but calls that may overlap on
- * the GPU (different streams, or several host threads) race and give wrong
- * time steps.  Asynchronous on `stream`; the host buffers it reads are
- * consumed before it returns. */
+ * (once per device, with the device current).  The call copies its box table
+ * from host memory that lives only for the call, so it refuses to run while
+ * `stream` is being captured into a CUDA graph (HYDRO_ERR_INVALID).  Every
+ * call on a device shares the one array: each call rewrites the box table
+ * and clears the per-box maxima before its kernels run, so calls ordered on
+ * one stream are safe, but calls that may overlap on the GPU (different
+ * streams, or several host threads) race and give wrong time steps.
+ * Asynchronous on `stream`; the host buffers it reads are consumed before it
+ * returns. */
 #define HYDRO_NOALLOC_MAX_BOXES 1024
 int hydro_compute_dt_noalloc(const hydro_box_desc* d, int nboxes, const double* state_dev, double* dt_dev,
                              void* stream);

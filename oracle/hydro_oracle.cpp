@@ -96,6 +96,29 @@ static const double FLAT_EPS = 0.33;
 static const double FLAT_OMEGA1 = 0.75;
 static const double FLAT_OMEGA2 = 10.0;
 
+/* Test instrumentation (no effect on any result).  Branch-hit counters: how
+ * often a step took each guard branch of the method, so that a test can show
+ * that a case really exercises it.  The wall switch turns R11 off, which a
+ * test uses to show that R11 changes FP64 results by rounding alone. */
+enum {
+  OB_HIT_PRIM_DENS_FLOOR = 0,  /* a2: rho < small_dens on a primitive copy */
+  OB_HIT_PRIM_PRES_FLOOR,      /* a2: p < small_pres */
+  OB_HIT_TRACE_DENS_FLOOR,     /* a5: traced rho < small_dens */
+  OB_HIT_TRACE_PRES_FLOOR,     /* a5: traced p < small_pres */
+  OB_HIT_DAVIS,                /* a9: Roe sound speed squared <= 0 (Davis bounds) */
+  OB_HIT_REVERT_STAGE1,        /* a7: corrected state with rho <= 0 or p <= 0 kept uncorrected */
+  OB_HIT_REVERT_STAGE2,        /* a8: the same in stage 2 */
+  OB_HIT_CORRECTED_PRES_FLOOR, /* a7/a8: 0 < corrected p < small_pres */
+  OB_NHITS
+};
+static long g_hits[OB_NHITS];
+static int g_wall_r11 = 1;
+
+static void hit(int k) {
+#pragma omp atomic
+  g_hits[k]++;
+}
+
 /* ------------------------------------------------------------------ grid */
 struct Grid {
   int n[3];
@@ -173,13 +196,19 @@ static void fill_ghosts(const ob_box* b, const Grid& G, double* U) {
 /* ---------------------------------------------------- a2: conserved -> primitive */
 static void cons_to_prim_zone(const double* U, long Z, long N, double gamma, double* q, double* c) {
   double rho = U[Z];
-  if (rho < SMALL_DENS) rho = SMALL_DENS;
+  if (rho < SMALL_DENS) {
+    rho = SMALL_DENS;
+    hit(OB_HIT_PRIM_DENS_FLOOR);
+  }
   double u = U[N + Z] / rho;
   double v = U[2 * N + Z] / rho;
   double w = U[3 * N + Z] / rho;
   double kin = 0.5 * rho * (u * u + v * v + w * w);
   double p = (gamma - 1.0) * (U[4 * N + Z] - kin);
-  if (p < SMALL_PRES) p = SMALL_PRES;
+  if (p < SMALL_PRES) {
+    p = SMALL_PRES;
+    hit(OB_HIT_PRIM_PRES_FLOOR);
+  }
   q[Z] = rho; q[N + Z] = u; q[2 * N + Z] = v; q[3 * N + Z] = w; q[4 * N + Z] = p;
   c[Z] = sqrt(gamma * p / rho);
 }
@@ -306,7 +335,7 @@ static double cs_interface(const double* a, long Z, long s) {
   if ((v - a0) * (a1 - v) < 0.0) {
     double d2 = 3.0 * (a0 - 2.0 * v + a1);
     double nb[2] = {am - 2.0 * a0 + a1, a0 - 2.0 * a1 + a2};
-    v = 0.5 * (a0 + a1) - cs_limited_d2(d2, nb, 2) * (1.0 / 6.0);
+    v = 0.5 * (a0 + a1) - cs_limited_d2(d2, nb, 2) / 6.0;
   }
   return v;
 }
@@ -417,8 +446,14 @@ static void trace_zone(const double* const qn[5], const double* const face[5], c
     out[0] = ref[0] - (beta[0] + beta[1] + beta[2]);
     out[1] = ref[1] - (cs / rho) * (beta[2] - beta[0]);
     out[4] = ref[4] - cs * cs * (beta[0] + beta[2]);
-    if (out[0] < SMALL_DENS) out[0] = SMALL_DENS;
-    if (out[4] < SMALL_PRES) out[4] = SMALL_PRES;
+    if (out[0] < SMALL_DENS) {
+      out[0] = SMALL_DENS;
+      hit(OB_HIT_TRACE_DENS_FLOOR);
+    }
+    if (out[4] < SMALL_PRES) {
+      out[4] = SMALL_PRES;
+      hit(OB_HIT_TRACE_PRES_FLOOR);
+    }
     double* dst = side == 0 ? qp : qm;
     for (int m = 0; m < 5; m++) dst[m] = out[m];
   }
@@ -447,6 +482,7 @@ static void hllc_normal(const double* L, const double* R, double gamma, double* 
   } else {
     SL = fmin(ul - cl, ur - cr);
     SR = fmax(ul + cl, ur + cr);
+    hit(OB_HIT_DAVIS);
   }
   double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur));
 
@@ -590,7 +626,11 @@ static int cons_to_prim_checked(const double* U, double gamma, double* q) {
   double p = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w));
   if (!(p > 0.0)) return 0;
   q[0] = U[0]; q[1] = u; q[2] = v; q[3] = w;
-  q[4] = p < SMALL_PRES ? SMALL_PRES : p;
+  if (p < SMALL_PRES) {
+    p = SMALL_PRES;
+    hit(OB_HIT_CORRECTED_PRES_FLOOR);
+  }
+  q[4] = p;
   return 1;
 }
 
@@ -727,7 +767,7 @@ static void corrected_state(const ob_box* b, const double* qin, int nterms, cons
     U[v] = val;
   }
   for (int v = 0; v < 5; v++) qout[v] = qin[v];
-  cons_to_prim_checked(U, b->gamma, qout);
+  if (!cons_to_prim_checked(U, b->gamma, qout)) hit(nterms == 1 ? OB_HIT_REVERT_STAGE1 : OB_HIT_REVERT_STAGE2);
 }
 
 static void ctu_stage1(const ob_box* b, const Grid& G, double dt, double* W) {
@@ -787,7 +827,8 @@ static void ctu_stage2(const ob_box* b, const Grid& G, double dt, double* W) {
           /* R11: a reflecting face is impermeable -- no mass, energy or
            * tangential momentum crosses it, only the pressure force acts */
           int face = d == 0 ? i : (d == 1 ? j : k);
-          if ((face == 0 && b->bc[2 * d] == OB_REFLECT) || (face == G.n[d] && b->bc[2 * d + 1] == OB_REFLECT)) {
+          if (g_wall_r11 &&
+              ((face == 0 && b->bc[2 * d] == OB_REFLECT) || (face == G.n[d] && b->bc[2 * d + 1] == OB_REFLECT))) {
             for (int v = 0; v < 5; v++)
               if (v != 1 + d) F[v] = 0.0;
           }
@@ -972,6 +1013,18 @@ void oracle_trace_line(const double* q, const double* c, const double* chi, int 
   free(dm);
   free(face);
 }
+
+/* Test instrumentation: branch-hit counters (OB_HIT_*, copied into out[0..n-1]
+ * and cleared when reset != 0) and the R11 switch (1 on, the default; 0 off).
+ * Neither changes what a step computes while R11 is on. */
+int oracle_branch_hits(long* out, int n, int reset) {
+  for (int k = 0; k < n && k < OB_NHITS; k++) out[k] = g_hits[k];
+  if (reset)
+    for (int k = 0; k < OB_NHITS; k++) g_hits[k] = 0;
+  return OB_NHITS;
+}
+
+void oracle_set_wall_r11(int on) { g_wall_r11 = on ? 1 : 0; }
 
 /* flattening coefficient of a 1D line along x: p[n], u[n]; zones 3..n-4 written */
 void oracle_flatten_line(const double* p, const double* u, int n, double* f) {

@@ -84,6 +84,8 @@ def lib():
             L.oracle_two_shock.argtypes = [_D, _D, ctypes.c_double, _D, _D, _D]
             L.oracle_riemann_star.argtypes = [ctypes.c_double] * 7 + [_D, _D]
             L.oracle_riemann_sample.argtypes = [ctypes.c_double] * 7 + [_D, ctypes.c_int, _D, _D, _D]
+            L.oracle_branch_hits.argtypes = [ctypes.POINTER(ctypes.c_long), ctypes.c_int, ctypes.c_int]
+            L.oracle_set_wall_r11.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -258,3 +260,20 @@ def riemann_sample(left, right, gamma: float, S):
 
 def pair_field(d: int, e: int) -> int:
     return W_F1 + 5 * PAIRS.index((d, e))
+
+
+# test instrumentation: which guard branches of the method a run took
+BRANCHES = ("prim_dens_floor", "prim_pres_floor", "trace_dens_floor", "trace_pres_floor", "davis",
+            "revert_stage1", "revert_stage2", "corrected_pres_floor")
+
+
+def branch_hits(reset: bool = True) -> dict:
+    """Counts of the guard branches taken since the last reset (and reset them)."""
+    out = (ctypes.c_long * len(BRANCHES))()
+    lib().oracle_branch_hits(out, len(BRANCHES), int(reset))
+    return dict(zip(BRANCHES, (int(v) for v in out)))
+
+
+def set_wall_r11(on: bool) -> None:
+    """R11 (impermeable reflecting faces) on (default) or off."""
+    lib().oracle_set_wall_r11(int(bool(on)))

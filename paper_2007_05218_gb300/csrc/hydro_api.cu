@@ -193,6 +193,21 @@ cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const do
 
 namespace hydro {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+int box_layouts(const hydro_box_desc* d, int nboxes, hydro_layout* out) {
+  if (!out) return fail(HYDRO_ERR_INVALID, "null output pointer");
+  Geometry g;
+  int rc = plan_geometry(d, nboxes, &g);
+  if (rc) return rc;
+  for (int i = 0; i < nboxes; i++) {
+    const HostBox& hb = g.boxes[i];
+    out[i].offset = hb.state_off;
+    out[i].pitch = hb.pitch;
+    out[i].plane = hb.plane;
+    out[i].var_stride = hb.vs;
+  }
+  return HYDRO_OK;
+}
 }  // namespace hydro
 
 namespace {

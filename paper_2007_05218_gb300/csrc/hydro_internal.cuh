@@ -197,6 +197,9 @@ extern const char* const TABLE_NAMES[NTABLES];
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream);
 // Sets the thread-local message returned by hydro_last_error (hydro_api.cu).
 void set_last_error(const std::string& msg);
+// Validates d[0..nboxes-1] and writes every box's place in the state buffer
+// (what hydro_box_layout gives for each box) in one pass (hydro_api.cu).
+int box_layouts(const hydro_box_desc* d, int nboxes, hydro_layout* out);
 cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream);
 
 }  // namespace hydro

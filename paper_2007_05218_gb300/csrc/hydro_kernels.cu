@@ -45,6 +45,7 @@
 
 #include "fp64_fast.cuh"
 #include "hydro_internal.cuh"
+#include "prim_zone.cuh"
 
 namespace hydro {
 namespace {
@@ -242,9 +243,9 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
     const long long vs = b.vs;
     const double* U = state + b.state_off;
     double rho = U[Z];
-    if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
     double u, v, w, p, cs, ir = 0.0, ic = 0.0;
     if constexpr (EXACT) {
+      if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
       u = __ddiv_rn(U[vs + Z], rho);
       v = __ddiv_rn(U[2 * vs + Z], rho);
       w = __ddiv_rn(U[3 * vs + Z], rho);
@@ -254,15 +255,15 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
       cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(b.gamma, p), rho));
     } else {
-      ir = nr_rcp(rho);
-      u = U[vs + Z] * ir;
-      v = U[2 * vs + Z] * ir;
-      w = U[3 * vs + Z] * ir;
-      p = (b.gamma - 1.0) * (U[4 * vs + Z] - 0.5 * rho * (u * u + v * v + w * w));
-      if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
-      const double c2 = b.gamma * p * ir;
-      ic = nr_rsqrt(c2);
-      cs = c2 * ic;
+      const PrimZone pz = prim_zone(rho, U[vs + Z], U[2 * vs + Z], U[3 * vs + Z], U[4 * vs + Z], b.gamma);
+      rho = pz.rho;
+      u = pz.u;
+      v = pz.v;
+      w = pz.w;
+      p = pz.p;
+      cs = pz.cs;
+      ir = pz.ir;
+      ic = pz.ic;
     }
     if (b.precision == HYDRO_FP64) {
       double* W = fields<double>(work, b);
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
       W[FLD_C * vs + Z] = (float)cs;
     }
     if (c[0] >= 0 && c[0] < b.n[0] && c[1] >= 0 && c[1] < b.n[1] && c[2] >= 0 && c[2] < b.n[2]) {
-      double s = dmax(dmax((fabs(u) + cs) * b.idx[0], (fabs(v) + cs) * b.idx[1]), (fabs(w) + cs) * b.idx[2]);
+      const double s = signal_rate(u, v, w, cs, b.idx);
       sbits = (unsigned long long)__double_as_longlong(s);
     }
   }
@@ -353,7 +354,45 @@ __global__ void __launch_bounds__(256) k_dt_shared(const DevBox* __restrict__ bo
   }
 }
 
+// CS08's branches (interface in bounds, zone or neighbour at an extremum,
+// second differences of one sign) are not continuous in their inputs: a
+// one-ulp change can move an edge value by the size of the limited
+// curvature.  So every quantity a branch depends on (the interface values
+// included) is formed with single IEEE operations (no contraction into fused
+// multiply-adds) in the order the method writes them, and equal inputs give
+// bitwise equal decisions on any IEEE machine.
+__device__ __forceinline__ double ie_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ie_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ie_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float ie_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double ie_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float ie_div(float a, float b) { return __fdiv_rn(a, b); }
+
 // ---------------------------------------------------------------- flattening
+// CW84's shock test |dp1| / min(p) > eps, a discontinuous decision.  FP64: the
+// same decision as the correctly rounded quotient compared with eps, without
+// a divide wherever the answer is clear: d = a - eps m from one multiply-add
+// has the exact sign of a/m - eps, and when |d| > 2^-48 a the quotient lies
+// more than 2^-48 (relative) away from eps, farther than its rounding can
+// move it; within that band (rare) the warp forms the quotient itself.
+// FP32 (mixed precision): the product form a > eps m.
+template <typename R>
+__device__ __forceinline__ bool flat_shock(R a, R m) {
+  if constexpr (Consts<R>::FP_BOUND) {
+    const R d = fma(-R(FLAT_EPS), m, a);
+    const bool near = !dgt(R(fabs(d)), a * R(0x1p-48));
+    bool r = is_pos(d);
+    if (any_in_warp<R>(near)) {
+      if (near) r = ie_div(a, m) > R(FLAT_EPS);
+    }
+    return r;
+  } else {
+    return dgt(a, R(FLAT_EPS) * m);
+  }
+}
+
 template <typename R>
 // (comparisons and min/max through the helpers: exact, and off the FP64 pipe;
 // the ratio dp1/dp2 only enters the clamped linear part, so the refined
@@ -361,7 +400,7 @@ template <typename R>
 __device__ __forceinline__ R flat_tilde(const R* __restrict__ p, const R* __restrict__ un, long long Z, long long s) {
   const R pp = p[Z + s], pm = p[Z - s];
   const R dp1 = pp - pm;
-  if (!dgt(R(fabs(dp1)), R(FLAT_EPS) * dmin(pp, pm)) || !is_pos(un[Z - s] - un[Z + s])) return R(0);
+  if (!flat_shock(R(fabs(dp1)), dmin(pp, pm)) || !is_pos(un[Z - s] - un[Z + s])) return R(0);
   const R dp2 = p[Z + 2 * s] - p[Z - 2 * s];
   if (!is_pos(fabs(dp2))) return R(0);
   return dmin(R(1), dmax(R(0), R(FLAT_OMEGA2) * (dp1 * nr_rcp(dp2) - R(FLAT_OMEGA1))));
@@ -505,19 +544,6 @@ __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, 
 // Curvature bound of CS08 (C = 1.25).
 constexpr double CS_C = 1.25;
 
-// CS08's branches (interface in bounds, zone or neighbour at an extremum,
-// second differences of one sign) are not continuous in their inputs: a
-// one-ulp change can move an edge value by the size of the limited
-// curvature.  So every quantity a branch depends on (the interface values
-// included) is formed with single IEEE operations (no contraction into fused
-// multiply-adds) in the order the method writes them, and equal inputs give
-// bitwise equal decisions on any IEEE machine.
-__device__ __forceinline__ double ie_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double ie_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double ie_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float ie_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
 
 // second difference a - 2 b + c, as (a - 2 b) + c
 template <typename R>
@@ -540,14 +566,15 @@ __device__ __forceinline__ R cs_limited_d2(R d2, const R* o) {
 // Value at the face between zones a0 and a1 (neighbours am, a2): the
 // 4th-order interpolant 7/12 (a0 + a1) - 1/12 (am + a2), rebuilt as
 // (a0 + a1)/2 - d2_lim/6 from the limited second difference d2 = 3 (a0 - 2v + a1)
-// when it does not lie between a0 and a1 (CS08 §2.1).
+// when it does not lie between a0 and a1 (CS08 §2.1; the division by 6 is a
+// correctly rounded divide, taken only on that branch).
 template <typename R>
 __device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
   R v = ie_sub(ie_mul(R(7.0 / 12.0), ie_add(a0, a1)), ie_mul(R(1.0 / 12.0), ie_add(am, a2)));
   if (opp_sign(ie_sub(v, a0), ie_sub(a1, v))) {
     const R d2 = ie_mul(R(3), ie_add(ie_sub(a0, ie_mul(R(2), v)), a1));
     const R o[2] = {ie_d2(am, a0, a1), ie_d2(a0, a1, a2)};
-    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_mul(cs_limited_d2<R, 2>(d2, o), R(1.0 / 6.0)));
+    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_div(cs_limited_d2<R, 2>(d2, o), R(6)));
   }
   return v;
 }

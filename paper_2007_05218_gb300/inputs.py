@@ -197,6 +197,57 @@ def uniform(n=8, rho=1.0, vel=(0.3, -0.2, 0.1), p=1.0, gamma=1.4, bc="periodic",
     return Problem("uniform", U, (1.0 / nx, 1.0 / ny, 1.0 / nz), gamma, cfl, (bc,) * 6, nsteps)
 
 
+def checkerboard(n=(8, 6, 4), rho0=1.0, amp=0.1, vel=(1.0, -0.6, 0.35), p=1e-4, gamma=1.4, cfl=0.9,
+                 nsteps=3) -> Problem:
+    """Density rho0 + amp (-1)^(i+j+k) carried by a uniform velocity at uniform
+    pressure, periodic; even extents, so that every zone is a local extremum
+    of the density along every axis (also across the periodic seams)."""
+    nx, ny, nz = _as_shape(n)
+    if nx % 2 or ny % 2 or nz % 2:
+        raise ValueError("checkerboard extents must be even")
+    shape = (nz, ny, nx)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rho = rho0 + amp * (1.0 - 2.0 * ((i + j + k) % 2))
+    U = _conserved(rho, np.full(shape, vel[0]), np.full(shape, vel[1]), np.full(shape, vel[2]),
+                   np.full(shape, p), gamma)
+    return Problem("checkerboard", U, (1.0 / nx, 1.0 / ny, 1.0 / nz), gamma, cfl, ("periodic",) * 6, nsteps,
+                   {"rho0": rho0, "amp": amp, "vel": tuple(vel), "p": p})
+
+
+def shear_cold(n=(16, 16, 8), seed=3, p=0.02, amp=0.5, gamma=1.4, cfl=0.5, nsteps=10) -> Problem:
+    """A low-pressure shear layer (rho 2 inside |y| < 1/4, else 1; u = +-1/2)
+    with large seeded velocity noise U(-amp, amp) on u, v, w: the transverse
+    corrections of some face states come out with p <= 0 on the first step.
+    Periodic x, z; reflecting y."""
+    nx, ny, nz = _as_shape(n)
+    shape = (nz, ny, nx)
+    y = _centres(ny, -0.5, 1.0 / ny)
+    inside = (np.abs(y) < 0.25)[None, :, None] & np.ones(shape, dtype=bool)
+    N = nx * ny * nz
+    ctr = np.arange(N, dtype=np.uint64) * np.uint64(3)
+    pert = [amp * (2.0 * uniform01(seed, 0, ctr + np.uint64(c)).reshape(shape) - 1.0) for c in range(3)]
+    rho = np.where(inside, 2.0, 1.0)
+    u = np.where(inside, 0.5, -0.5) + pert[0]
+    U = _conserved(rho, u, pert[1], pert[2], np.full(shape, p), gamma)
+    return Problem("shear_cold", U, (1.0 / nx, 1.0 / ny, 1.0 / nz), gamma, cfl,
+                   ("periodic", "periodic", "reflect", "reflect", "periodic", "periodic"), nsteps, {"seed": seed})
+
+
+def vacuum_ball(n=(16, 16, 16), radius=0.3, rho_vac=1e-14, p_vac=1e-14, gamma=1.4, cfl=0.5,
+                nsteps=10) -> Problem:
+    """A ball of gas at rest (rho = 1, p = 1, radius `radius` on [-1/2,1/2]^3)
+    in a near vacuum whose density and pressure lie below the method's floors;
+    outflow boundaries."""
+    nx, ny, nz = _as_shape(n)
+    shape = (nz, ny, nx)
+    x, y, z = _centres(nx, -0.5, 1.0 / nx), _centres(ny, -0.5, 1.0 / ny), _centres(nz, -0.5, 1.0 / nz)
+    r2 = z[:, None, None] ** 2 + y[None, :, None] ** 2 + x[None, None, :] ** 2
+    inside = r2 < radius * radius
+    zero = np.zeros(shape)
+    U = _conserved(np.where(inside, 1.0, rho_vac), zero, zero, zero, np.where(inside, 1.0, p_vac), gamma)
+    return Problem("vacuum_ball", U, (1.0 / nx, 1.0 / ny, 1.0 / nz), gamma, cfl, ("outflow",) * 6, nsteps)
+
+
 BATCH_EDGES = (16, 24, 32, 48, 64)
 
 

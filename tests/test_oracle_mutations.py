@@ -14,9 +14,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
-PIN_TESTS = ["tests/test_oracle_riemann.py", "tests/test_oracle_stages.py", "tests/test_oracle_scheme.py",
-             "tests/test_oracle_variants.py"]
-VARIANT_PINS_FIRST = PIN_TESTS[3:] + PIN_TESTS[:3]
+PIN_TESTS = ["tests/test_oracle_ctu.py", "tests/test_oracle_riemann.py", "tests/test_oracle_stages.py",
+             "tests/test_oracle_scheme.py", "tests/test_oracle_variants.py"]
+VARIANT_PINS_FIRST = PIN_TESTS[4:] + PIN_TESTS[:4]
 
 # (name, file, original text, planted mistake)
 MUTANTS = [
@@ -78,6 +78,29 @@ MUTANTS = [
      "q[m] = (1.0 - a) * outer[m] + a * star[m];", "q[m] = a * outer[m] + (1.0 - a) * star[m];"),
     ("two-shock fan tail uses the outer sound speed", "hydro_oracle.cpp",
      "tail = sqrt(gamma * ps / rs) - sgn * us;", "tail = sqrt(gamma * pk / rk) - sgn * us;"),
+    ("CTU stage-1 factor 1/2 instead of 1/3", "hydro_oracle.cpp",
+     "double fac = dt / (3.0 * b->dx[e]);", "double fac = dt / (2.0 * b->dx[e]);"),
+    ("CTU stage-2 factor 1/3 instead of 1/2", "hydro_oracle.cpp",
+     "double fac[2] = {dt / (2.0 * b->dx[e]), dt / (2.0 * b->dx[f])};",
+     "double fac[2] = {dt / (3.0 * b->dx[e]), dt / (3.0 * b->dx[f])};"),
+    ("CTU stage-2 fluxes corrected along the face's own axis", "hydro_oracle.cpp",
+     "W_F1 + 5 * pair_index(e, f)) * N,\n                           W + (long)(W_F1 + 5 * pair_index(f, e)) * N};",
+     "W_F1 + 5 * pair_index(e, d)) * N,\n                           W + (long)(W_F1 + 5 * pair_index(f, d)) * N};"),
+    ("CTU stage-2 pairs swapped", "hydro_oracle.cpp",
+     "W_F1 + 5 * pair_index(e, f)) * N,\n                           W + (long)(W_F1 + 5 * pair_index(f, e)) * N};",
+     "W_F1 + 5 * pair_index(f, e)) * N,\n                           W + (long)(W_F1 + 5 * pair_index(e, f)) * N};"),
+    ("CTU revert rule dropped for p <= 0", "hydro_oracle.cpp",
+     "if (!(p > 0.0)) return 0;", "if (!(p > -1e300)) return 0;"),
+    ("flattening threshold eps 0.5", "hydro_oracle.cpp",
+     "static const double FLAT_EPS = 0.33;", "static const double FLAT_EPS = 0.5;"),
+    ("flattening omega1 0.85", "hydro_oracle.cpp",
+     "static const double FLAT_OMEGA1 = 0.75;", "static const double FLAT_OMEGA1 = 0.85;"),
+    ("flattening omega2 5", "hydro_oracle.cpp",
+     "static const double FLAT_OMEGA2 = 10.0;", "static const double FLAT_OMEGA2 = 5.0;"),
+    ("flattening tie takes the other neighbour", "hydro_oracle.cpp",
+     "long sh = dp1 >= 0.0 ? s : -s;", "long sh = dp1 > 0.0 ? s : -s;"),
+    ("tracing reference state is the zone value", "hydro_oracle.cpp",
+     "int reaches_fast = side == 0 ? lam[2] > 0.0 : lam[0] < 0.0;", "int reaches_fast = 0;"),
 ]
 
 
