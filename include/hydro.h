@@ -224,11 +224,14 @@ int hydro_set_method(hydro_handle* h, int limiter, int riemann);
  * simulated time (it refills ghosts and recomputes intermediates only), and
  * synchronises `stream` before returning. */
 typedef struct hydro_tuning {
-  char name[24];      /* fill_x, fill_y, fill_z, prim, flatten, slopes, trace, riemann, ctu1, ctu2 */
+  char name[24];      /* fill_x, fill_y, fill_z, prim, flatten, slopes, trace, riemann, ctu1, ctu2, the line
+                         tables, tile */
   int32_t precision;  /* HYDRO_FP64 or HYDRO_MIXED kernels */
-  int32_t threads;    /* chosen threads per block */
+  int32_t threads;    /* chosen threads per block (tile: 32 x (rows + 2)) */
   int32_t order;      /* 0: boxes in the given order, 1: largest work item first */
   float ms;           /* time of one launch with that choice */
+  int32_t tile_rows;  /* tile: interior zone rows per tile (30 zones each); else 0 */
+  int32_t tile_seg;   /* tile: z-planes per segment (0: the whole box); else 0 */
 } hydro_tuning;
 int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries, int* nentries, void* stream);
 int hydro_use_graphs(hydro_handle* h, int enable);
@@ -248,6 +251,21 @@ int hydro_use_graphs(hydro_handle* h, int enable);
  * On by default; hydro_fuse_lines(h, 0) runs the separate stages. */
 int hydro_fuse_lines(hydro_handle* h, int enable);
 
+/* Fused tile stage.  For HYDRO_MIXED boxes under HYDRO_LIMITER_CW84 one
+ * kernel replaces the slope, tracing, Riemann, CTU and update stages: a block
+ * advances a tile of 30 x rows interior zone columns of a box (with a one-zone
+ * halo, 32 x (rows + 2) threads) over a segment of z-planes, marching in z
+ * with the primitive state of each plane staged in shared memory and every
+ * traced state and flux of the step kept on chip, then applies the FP64
+ * update.  The results are bitwise those of the line stage (same arithmetic).
+ * hydro_fuse_tiles(h, 1) switches it on (hydro_fuse_lines then applies to
+ * nothing); hydro_autotune picks the tile rows (2 or 6) and the segment length
+ * (16, 32, 64 planes or the whole box) and the box order by timing them;
+ * hydro_set_tile_shape sets them directly (seg 0: the whole box).  Stage time
+ * "tile" in hydro_profile_end.  Off by default. */
+int hydro_fuse_tiles(hydro_handle* h, int enable);
+int hydro_set_tile_shape(hydro_handle* h, int rows, int seg);
+
 /* Number of kernels this handle has launched since hydro_alloc (a ghost fill
  * is three kernels, every other stage one per compute type present), into
  * *count. */
@@ -265,6 +283,13 @@ typedef struct hydro_stage_time {
 } hydro_stage_time;
 int hydro_profile_begin(hydro_handle* h);
 int hydro_profile_end(hydro_handle* h, hydro_stage_time* out, int max_stages, int* nstages);
+
+/* Pipe-rate probes (diagnostics for rooflines): the measured FP64 and FP32
+ * fused multiply-add rates of the current device, in flop/s (a multiply-add
+ * counts 2), from two launches of kernels that do nothing but independent
+ * multiply-add chains on every SM (about 0.3 s in all), and the device's SM
+ * count.  Synchronous on `stream`. */
+int hydro_measure_peaks(double* fp64_flops_per_s, double* fp32_flops_per_s, int32_t* sms, void* stream);
 
 /* ---- time steps without any allocation by the caller ----
  * The paper has no counterpart to this call; it exists for callers that

@@ -579,12 +579,118 @@ int hydro_fuse_lines(hydro_handle* h, int enable) {
   return HYDRO_OK;
 }
 
+int hydro_fuse_tiles(hydro_handle* h, int enable) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (enable) {
+    cudaError_t e = hydro::prepare_tile_kernels();
+    if (e != cudaSuccess) return cuda_fail(e, "hydro_fuse_tiles");
+  }
+  h->plan.fuse_tiles = enable != 0;
+  return launched(upload_table(h, hydro::TB_TILE, 1), "hydro_fuse_tiles");
+}
+
+int hydro_set_tile_shape(hydro_handle* h, int rows, int seg) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  if (rows != hydro::TILE_TYS[0] && rows != hydro::TILE_TYS[1])
+    return fail(HYDRO_ERR_INVALID, "hydro_set_tile_shape: rows must be 2 or 6");
+  if (seg < 0) return fail(HYDRO_ERR_INVALID, "hydro_set_tile_shape: seg must be >= 0");
+  int rc = check_device(h);
+  if (rc) return rc;
+  h->plan.tile_ty = rows;
+  h->plan.tile_seg = seg;
+  return launched(upload_table(h, hydro::TB_TILE, 1), "hydro_set_tile_shape");
+}
+
 int hydro_use_graphs(hydro_handle* h, int enable) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
   h->use_graphs = enable != 0;
   if (!h->use_graphs) drop_graph(h);
   return HYDRO_OK;
 }
+
+namespace {
+
+// The state of every FP32 box copied into (or back from) its scratch fields
+// that the fused tile stage leaves unused (from the traced-state fields on).
+cudaError_t save_mixed_state(hydro_handle* h, bool restore, cudaStream_t s) {
+  const hydro::Plan& p = h->plan;
+  for (int b = 0; b < p.nboxes; b++) {
+    const HostBox& hb = h->boxes[b];
+    if (hb.d.precision != HYDRO_MIXED) continue;
+    double* st = p.state + hb.state_off;
+    unsigned char* bk = p.work + hb.work_off + (size_t)hydro::FLD_QM * hb.vs * sizeof(float);
+    const size_t bytes = 5 * (size_t)hb.vs * sizeof(double);
+    cudaError_t e = restore ? cudaMemcpyAsync(st, bk, bytes, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(bk, st, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Tile rows, z-segment length and box order of the fused tile stage: every
+// combination timed over `reps` launches (each launch updates the state, which
+// is saved before and restored after), the fastest kept.
+cudaError_t tune_tiles(hydro_handle* h, int reps, cudaStream_t s, cudaEvent_t* ev, hydro_tuning* out, int max_entries,
+                       int* n) {
+  hydro::Plan& p = h->plan;
+  hydro::WorkTable& w = p.tab[hydro::TB_TILE][1];
+  const int segs[4] = {16, 32, 64, 0};
+  int best_ty = p.tile_ty, best_seg = p.tile_seg, best_order = w.order;
+  float best_ms = 0.f;
+  bool first = true;
+  // the repeated updates may flag states nonphysical: the runtime records
+  // (status flags) are saved and restored too
+  std::vector<BoxRt> rt_saved(p.nboxes);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(rt_saved.data(), p.rt, sizeof(BoxRt) * p.nboxes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = save_mixed_state(h, false, s);
+  for (int ti = 0; ti < 2 && e == cudaSuccess; ti++)
+    for (int si = 0; si < 4 && e == cudaSuccess; si++)
+      for (int o = 0; o < 2 && e == cudaSuccess; o++) {
+        p.tile_ty = hydro::TILE_TYS[ti];
+        p.tile_seg = segs[si];
+        w.order = o;
+        e = upload_table(h, hydro::TB_TILE, 1);
+        if (e == cudaSuccess) e = hydro::launch_table(p, hydro::TB_TILE, 1, s);  // warm
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        for (int r = 0; r < reps && e == cudaSuccess; r++) e = hydro::launch_table(p, hydro::TB_TILE, 1, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        ms /= reps;
+        if (e == cudaSuccess && (first || ms < best_ms)) {
+          best_ms = ms;
+          best_ty = p.tile_ty;
+          best_seg = p.tile_seg;
+          best_order = o;
+          first = false;
+        }
+      }
+  if (e == cudaSuccess) e = save_mixed_state(h, true, s);
+  p.tile_ty = best_ty;
+  p.tile_seg = best_seg;
+  w.order = best_order;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(p.rt, rt_saved.data(), sizeof(BoxRt) * p.nboxes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload_table(h, hydro::TB_TILE, 1);
+  if (e == cudaSuccess && *n < max_entries) {
+    memset(&out[*n], 0, sizeof out[*n]);
+    snprintf(out[*n].name, sizeof out[*n].name, "%s", hydro::TABLE_NAMES[hydro::TB_TILE]);
+    out[*n].precision = HYDRO_MIXED;
+    out[*n].threads = 32 * (best_ty + 2);
+    out[*n].order = best_order;
+    out[*n].ms = best_ms;
+    out[*n].tile_rows = best_ty;
+    out[*n].tile_seg = best_seg;
+  }
+  (*n)++;
+  return e;
+}
+
+}  // namespace
 
 int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries, int* nentries, void* stream) {
   if (!h || !nentries || (max_entries > 0 && !out)) return fail(HYDRO_ERR_INVALID, "null argument");
@@ -608,7 +714,7 @@ int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries
   const int order[] = {hydro::TB_FILL_X,  hydro::TB_FILL_Y,  hydro::TB_FILL_Z, hydro::TB_PRIM,
                        hydro::TB_FLATTEN, hydro::TB_SLOPES,  hydro::TB_TRACE,  hydro::TB_RIEMANN,
                        hydro::TB_LINE_X,  hydro::TB_LINE_YZ, hydro::TB_CTU1,   hydro::TB_CTU1_LINE,
-                       hydro::TB_CTU2,    hydro::TB_CTU2_LINE};
+                       hydro::TB_CTU2,    hydro::TB_CTU2_LINE, hydro::TB_TILE};
   for (int t : order) {
     for (int sl = 0; sl < 2; sl++) {
       hydro::WorkTable& w = p.tab[t][sl];
@@ -619,6 +725,13 @@ int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries
                         t == hydro::TB_CTU2_LINE;
       const bool replaced = t == hydro::TB_SLOPES || t == hydro::TB_TRACE || t == hydro::TB_RIEMANN ||
                             t == hydro::TB_CTU1 || t == hydro::TB_CTU2;
+      if (t == hydro::TB_TILE) {
+        if (!hydro::tile_fused(p, sl)) continue;
+        e = tune_tiles(h, reps, s, ev, out, max_entries, &n);
+        if (e != cudaSuccess) break;
+        continue;
+      }
+      if (hydro::tile_fused(p, sl) && (line || replaced)) continue;
       if (line ? !fused : fused && replaced) continue;
       int best_tpb = w.tpb, best_order = w.order;
       float best_ms = 0.f;

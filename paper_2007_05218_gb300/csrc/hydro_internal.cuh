@@ -110,12 +110,16 @@ enum TableId : int {
   TB_LINE_YZ,  // the same along y (item z = 0) and z (item z = 1)
   TB_CTU2_LINE,  // CTU stage 2 by zones along lines (FP32 boxes)
   TB_CTU1_LINE,  // CTU stage 1 by zones along lines (FP32 boxes)
+  TB_TILE,       // fused tile stage: tracing, CTU, solves and update per z-marching tile (FP32 boxes)
   NTABLES
 };
-constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 1, 2, 3, 6};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 1, 2, 3, 6, 1};
 // tables of the precision-specific stage kernels exist once per compute type
 constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true,
-                                               true, true, true, true};
+                                               true, true, true, true, true};
+// tile shapes of the fused tile stage: 30 x TILE_TY[k] interior zone columns
+// per block (32 x (TY + 2) threads), marching over z-segments of a chosen length
+constexpr int TILE_TYS[2] = {2, 6};
 // the fused line stage runs for FP32 boxes only (slot 1): the FP64 stages are
 // bound by the FP64 pipe, which fusion does not relieve
 constexpr bool LINE_FUSED_SLOT[2] = {false, true};
@@ -152,11 +156,28 @@ struct Plan {
   int limiter = HYDRO_LIMITER_CW84;   // reconstruction variant of every box
   int riemann = HYDRO_RIEMANN_HLLC;   // Riemann solver of every box
   bool fuse_lines = true;             // fused line stage for FP32 boxes (CW84 limiter)
+  bool fuse_tiles = false;            // fused tile stage for FP32 boxes (CW84 limiter)
+  int tile_ty = 6;                    // tile rows (one of TILE_TYS)
+  int tile_seg = 64;                  // z-planes per tile segment (0: the whole box)
 };
+
+// Whether precision slot `slot` runs the fused tile stage under this plan
+// (it replaces the slope, tracing, Riemann, CTU and update stages there).
+inline bool tile_fused(const Plan& p, int slot) {
+  return LINE_FUSED_SLOT[slot] && p.fuse_tiles && p.limiter == HYDRO_LIMITER_CW84;
+}
 
 // Whether precision slot `slot` runs the fused line stage under this plan.
 inline bool line_fused(const Plan& p, int slot) {
-  return LINE_FUSED_SLOT[slot] && p.fuse_lines && p.limiter == HYDRO_LIMITER_CW84;
+  return LINE_FUSED_SLOT[slot] && p.fuse_lines && p.limiter == HYDRO_LIMITER_CW84 && !tile_fused(p, slot);
+}
+
+// Blocks of the fused tile stage for one box: tiles of 30 x ty columns times
+// z-segments of seg planes (seg <= 0: one segment).
+inline long long tile_blocks(const hydro_box_desc& d, int ty, int seg) {
+  const long long ntx = (d.nx + 29) / 30, nty = (d.ny + ty - 1) / ty;
+  const int sl = seg > 0 ? seg : d.nz;
+  return ntx * nty * ((d.nz + sl - 1) / sl);
 }
 
 // Threads per block each table starts with (before any autotuning).
@@ -179,6 +200,7 @@ enum Stage : int {
   ST_RIEMANN,
   ST_CTU1,
   ST_CTU2,
+  ST_TILE,
   ST_UPDATE,
   NSTAGES
 };
@@ -201,5 +223,8 @@ void set_last_error(const std::string& msg);
 // (what hydro_box_layout gives for each box) in one pass (hydro_api.cu).
 int box_layouts(const hydro_box_desc* d, int nboxes, hydro_layout* out);
 cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream);
+// Allows the fused tile kernels their dynamic shared memory (once per
+// process; call outside stream capture).
+cudaError_t prepare_tile_kernels();
 
 }  // namespace hydro

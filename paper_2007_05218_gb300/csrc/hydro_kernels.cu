@@ -1797,10 +1797,12 @@ __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict_
   }
 }
 
+// skip_mixed: FP32 boxes are updated by the fused tile stage
 __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __restrict__ boxes,
                                                 BoxRt* __restrict__ rt, double* __restrict__ state,
-                                                unsigned char* __restrict__ work) {
+                                                unsigned char* __restrict__ work, int skip_mixed) {
   LOCATE(tv)
+  if (skip_mixed && b.precision == HYDRO_MIXED) return;
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
@@ -1817,6 +1819,548 @@ __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __re
   // a momentum makes e2 NaN)
   const double e2 = 2.0 * nu[0] * nu[4] - m2;
   if (!is_pos(nu[0]) || !is_pos(e2) || e2 != e2) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+}
+
+// ---------------------------------------------------------- fused tile stage
+// For FP32 boxes under the CW84 limiter, one kernel does what the line, CTU
+// and update kernels do, with every traced state and flux of the step kept
+// on chip.  A block advances a tile of TILE_X x TY interior zone columns of
+// one box over a segment of z-planes, marching in z.  At plane p it stages
+// the primitive state of the plane (with a three-zone halo) in shared memory,
+// traces plane p along x, y and z, forms plane p's normal fluxes and the
+// stage-1 fluxes through its low z-face, then stage 1 in the plane and the
+// final fluxes of plane p-1, and applies the FP64 update to plane p-2.  A
+// thread owns one zone column of the tile with its one-zone halo (32 x (TY+2)
+// columns: a warp covers a row, lane l the zone x0 - 1 + l), keeps the z
+// stencil of its column in registers and exchanges in-plane neighbours
+// through shared memory and warp shuffles.  Each state and flux is formed by
+// the same functions from the same operands as in the line kernels and the
+// zone-wise CTU kernels, so the results are bitwise the same; the halo costs
+// (TY + 2) x 32 / (TY x 30) times the zone work and 3 planes of pipeline
+// warm-up per segment.
+constexpr int TILE_X = 30;
+
+template <int TY>
+struct TileShape {
+  static constexpr int NR = 32 * (TY + 2);  // threads = traced zones of a plane
+  static constexpr int QX = 36;             // staged zones along x: -3 .. 32
+  static constexpr int NQ = QX * (TY + 6);  // staged zones of a plane
+  // shared-memory layout (floats)
+  static constexpr int O_Q = 0;                 // q[5][NQ] of the plane being traced
+  static constexpr int O_C = O_Q + 5 * NQ;      // c[NR]
+  static constexpr int O_CHI = O_C + NR;        // chi[NR]
+  static constexpr int O_TX = O_CHI + NR;       // x-traced qm[5], qp[5]: [2 plane parities][10][NR]
+  static constexpr int O_TY = O_TX + 20 * NR;   // y-traced, likewise
+  static constexpr int O_TZ = O_TY + 20 * NR;   // z-traced, likewise (a thread's own column)
+  static constexpr int O_F0X = O_TZ + 20 * NR;  // normal fluxes [2][5][NR], conserved x,y,z components
+  static constexpr int O_F0Y = O_F0X + 10 * NR;
+  static constexpr int O_F0Z = O_F0Y + 10 * NR;  // by face parity
+  static constexpr int O_FZX = O_F0Z + 10 * NR;  // stage-1 z-face fluxes F^{z|x}, F^{z|y}: [2][5][NR]
+  static constexpr int O_FZY = O_FZX + 10 * NR;
+  static constexpr int O_F1 = O_FZY + 10 * NR;   // stage-1 in-plane fluxes [4][5][NR]: x|y, x|z, y|x, y|z
+  static constexpr int O_EX = O_F1 + 20 * NR;    // y exchange of corrected right-edge states: [2][7][NR]
+  static constexpr int O_FX = O_EX + 14 * NR;    // final x and y fluxes of the previous plane [5][NR] each
+  static constexpr int O_FY = O_FX + 5 * NR;
+  static constexpr int TOTAL = O_FY + 5 * NR;
+  static constexpr size_t BYTES = TOTAL * sizeof(float);
+};
+
+// A corrected edge state: primitive q, total energy and 1/sqrt(rho) (0 in FP32).
+struct EdgeF {
+  float q[5];
+  float E, rs;
+};
+
+// An edge state q (raw, normal frame of D) corrected by NT flux differences
+// dlt with factors fac, as ctu1_correct / ctu2_correct correct each edge.
+template <int NT>
+__device__ __forceinline__ EdgeF tile_correct1(const float* q, const float (*dlt)[5], const float* fac, float gamma,
+                                               float igm1) {
+  EdgeF e;
+  float u[4];
+#pragma unroll
+  for (int m = 0; m < 5; m++) e.q[m] = q[m];
+  conserved_of(e.q, igm1, u);
+  e.E = correct_by<float, NT>(e.q, u, dlt, fac, gamma, igm1, e.rs);
+  return e;
+}
+
+// Both edge states of a zone corrected by the same flux differences.
+template <int NT>
+__device__ __forceinline__ void tile_correct(const float* qm, const float* qp, const float (*dlt)[5], const float* fac,
+                                             float gamma, float igm1, EdgeF& em, EdgeF& ep) {
+  em = tile_correct1<NT>(qm, dlt, fac, gamma, igm1);
+  ep = tile_correct1<NT>(qp, dlt, fac, gamma, igm1);
+}
+
+// Riemann flux between two corrected states, in the normal frame of D.
+template <int RS>
+__device__ __forceinline__ void tile_flux(const EdgeF& l, const EdgeF& r, float gamma, float igm1, float* Fn) {
+  riemann<float, RS>(l.q, l.E, l.rs, r.q, r.E, r.rs, gamma, igm1, Fn);
+}
+
+// Flux difference across a zone for the normal frame of D: F[comp<D>(m)] at
+// the high face minus the low face.
+template <int D>
+__device__ __forceinline__ void tile_delta(const float* F, int NRr, int lo, int hi, float* d) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) d[m] = F[comp<D>(m) * NRr + hi] - F[comp<D>(m) * NRr + lo];
+}
+
+template <int D>
+__device__ __forceinline__ void tile_store(float* F, int NRr, int at, const float* Fn) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) F[comp<D>(m) * NRr + at] = Fn[m];
+}
+
+// Shuffle a corrected state from the lane below.
+__device__ __forceinline__ EdgeF shfl_up_edge(const EdgeF& e) {
+  EdgeF o;
+#pragma unroll
+  for (int m = 0; m < 5; m++) o.q[m] = __shfl_up_sync(0xffffffffu, e.q[m], 1);
+  o.E = __shfl_up_sync(0xffffffffu, e.E, 1);
+  o.rs = __shfl_up_sync(0xffffffffu, e.rs, 1);
+  return o;
+}
+
+__device__ __forceinline__ void put_edge(float* X, int NRr, int at, const EdgeF& e) {
+#pragma unroll
+  for (int m = 0; m < 5; m++) X[m * NRr + at] = e.q[m];
+  X[5 * NRr + at] = e.E;
+  X[6 * NRr + at] = e.rs;
+}
+
+__device__ __forceinline__ EdgeF get_edge(const float* X, int NRr, int at) {
+  EdgeF e;
+#pragma unroll
+  for (int m = 0; m < 5; m++) e.q[m] = X[m * NRr + at];
+  e.E = X[5 * NRr + at];
+  e.rs = X[6 * NRr + at];
+  return e;
+}
+
+// The PPM parabola of zone 0 of a line a[-2..2] (stride 1 in the array passed):
+// van Leer slopes of zones -1, 0, 1, interface values, CW84 limiter with
+// flattening f; as the line kernels form it.
+__device__ __forceinline__ void tile_parabola(float am2, float am1, float a0, float ap1, float ap2, float f, float& aL,
+                                              float& aR) {
+  const float dm1 = vl_slope(am2, am1, a0), d0 = vl_slope(am1, a0, ap1), dp1 = vl_slope(a0, ap1, ap2);
+  aL = ppm_face(am1, a0, dm1, d0);
+  aR = ppm_face(a0, ap1, d0, dp1);
+  cw84_limit(a0, f, aL, aR);
+}
+
+// Reflecting face of the box (impermeable: only the normal momentum flux
+// remains), as ctu2_flux decides it.
+template <int D>
+__device__ __forceinline__ void tile_wall(const DevBox& b, int face, float* Fn) {
+  const bool wall = (face == 0 && b.bc[2 * D] == HYDRO_BC_REFLECT && b.nbr1[2 * D] == 0) ||
+                    (face == b.n[D] && b.bc[2 * D + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * D + 1] == 0);
+  if (wall) {
+    Fn[0] = 0.0f;
+    Fn[2] = 0.0f;
+    Fn[3] = 0.0f;
+    Fn[4] = 0.0f;
+  }
+}
+
+template <int TY, int RS>
+__global__ void __launch_bounds__(TileShape<TY>::NR, 1)
+    k_tile(TableView tv, const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, double* __restrict__ state,
+           unsigned char* __restrict__ work, int seg_len) {
+  using T = TileShape<TY>;
+  constexpr int NR = T::NR, NQ = T::NQ;
+  extern __shared__ float sm[];
+  LOCATE(tv)
+  if (!box_uses<float>(b)) return;
+  const int nx = b.n[0], ny = b.n[1], nz = b.n[2];
+  const int ntx = (nx + TILE_X - 1) / TILE_X, nty = (ny + TY - 1) / TY, nseg = (nz + seg_len - 1) / seg_len;
+  const int vb = (int)(t_ / NR);
+  if (vb >= ntx * nty * nseg) return;  // whole blocks only
+  const int tx = vb % ntx, ty = (vb / ntx) % nty, seg = vb / (ntx * nty);
+  const int x0 = tx * TILE_X, y0 = ty * TY, z0 = seg * seg_len, z1 = min(z0 + seg_len, nz);
+  const int t = threadIdx.x, lane = t & 31;
+  const int ci = lane - 1, cj = (t >> 5) - 1;
+  const int gx = x0 + ci, gy = y0 + cj;
+  // a traced zone of the box; a zone of the tile's interior (and of the box);
+  // the low x- or y-face of this zone is one of the box's faces
+  const bool in_x = gx >= -1 && gx <= nx, in_y = gy >= -1 && gy <= ny;
+  const bool int_x = ci >= 0 && ci < TILE_X && gx < nx, int_y = cj >= 0 && cj < TY && gy < ny;
+  const bool fc_x = ci >= 0 && gx <= nx, fc_y = cj >= 0 && gy <= ny;
+  const long long vs = b.vs;
+  float* W = fields<float>(work, b);
+  double* U = state + b.state_off;
+  const BoxRt& r = rt[bi];
+  const float gamma = b.gamma_f, igm1 = b.igm1_f;
+  const float dtdx[3] = {r.dtdx_f[0], r.dtdx_f[1], r.dtdx_f[2]};
+  const double dtdx64[3] = {r.dt * b.idx[0], r.dt * b.idx[1], r.dt * b.idx[2]};
+  const float fac1[3] = {dtdx[0] * float(1.0 / 3.0), dtdx[1] * float(1.0 / 3.0), dtdx[2] * float(1.0 / 3.0)};
+  float* sQ = sm + T::O_Q;
+  float* sC = sm + T::O_C;
+  float* sChi = sm + T::O_CHI;
+  // zone of the state/fields at (x, y, k), with x and y clamped into the ghosted box
+  auto zat = [&](int x, int y, int k) {
+    return zone(b, min(max(x, -NG), nx + NG - 1), min(max(y, -NG), ny + NG - 1), k);
+  };
+  const long long Zc = zat(gx, gy, 0) - (long long)NG * b.s[2];  // this column at k = 0 is Zc + (k+NG) s_z
+  const long long sz = b.s[2];
+
+  // z stencil of this column, as line_walk keeps it: zone values of the next
+  // three planes, the slope of the next plane and the value at its low face
+  float q0[5], q1[5], q2[5], d0[5], fl[5];
+  {
+    const int k = z0 - 1;  // the first plane traced
+    const long long Z = Zc + (long long)(k + NG) * sz;
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+      const float* a = W + comp<2>(m) * vs + Z;
+      const float qa = a[-2 * sz], qb = a[-sz];
+      q0[m] = a[0];
+      q1[m] = a[sz];
+      q2[m] = a[2 * sz];
+      const float db = vl_slope(qa, qb, q0[m]);
+      d0[m] = vl_slope(qb, q0[m], q1[m]);
+      fl[m] = ppm_face(qb, q0[m], db, d0[m]);
+    }
+  }
+  EdgeF zfin;                         // U^{z,fin} right edge of the plane before the one being finished
+  float fz_prev[5] = {0, 0, 0, 0, 0};  // final flux through the low z-face of the plane before
+  zfin.E = zfin.rs = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 5; m++) zfin.q[m] = 0.0f;
+
+#pragma unroll 1
+  for (int p = z0 - 1; p <= z1 + 1; p++) {
+    const bool trace = p <= z1;
+    const int cur = p & 1, prv = cur ^ 1;
+    float* tx_c = sm + T::O_TX + cur * 10 * NR;
+    float* tx_p = sm + T::O_TX + prv * 10 * NR;
+    float* ty_c = sm + T::O_TY + cur * 10 * NR;
+    float* ty_p = sm + T::O_TY + prv * 10 * NR;
+    float* tz_c = sm + T::O_TZ + cur * 10 * NR;
+    float* tz_p = sm + T::O_TZ + prv * 10 * NR;
+    float* f0x_c = sm + T::O_F0X + cur * 5 * NR;
+    float* f0x_p = sm + T::O_F0X + prv * 5 * NR;
+    float* f0y_c = sm + T::O_F0Y + cur * 5 * NR;
+    float* f0y_p = sm + T::O_F0Y + prv * 5 * NR;
+    float* f0z_c = sm + T::O_F0Z + cur * 5 * NR;
+    float* f0z_p = sm + T::O_F0Z + prv * 5 * NR;
+    float* fzx_c = sm + T::O_FZX + cur * 5 * NR;
+    float* fzx_p = sm + T::O_FZX + prv * 5 * NR;
+    float* fzy_c = sm + T::O_FZY + cur * 5 * NR;
+    float* fzy_p = sm + T::O_FZY + prv * 5 * NR;
+    float* sF1 = sm + T::O_F1;
+    float* ex0 = sm + T::O_EX;
+    float* ex1 = sm + T::O_EX + 7 * NR;
+    float* sFX = sm + T::O_FX;
+    float* sFY = sm + T::O_FY;
+
+    // state of the plane the update reaches this step, requested early
+    const int pu = p - 2;
+    const bool upd = pu >= z0 && pu < z1 && int_x && int_y;
+    double uo[5];
+    const long long Zu = Zc + (long long)(pu + NG) * sz;
+    if (upd) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) uo[v] = U[v * vs + Zu];
+    }
+
+    // 1. stage plane p: primitive state with a three-zone halo, c and chi
+    if (trace) {
+      for (int e = t; e < NQ; e += NR) {
+        const int qi = e % T::QX - 3, qj = e / T::QX - 3;
+        const long long Z = zat(x0 + qi, y0 + qj, p);
+#pragma unroll
+        for (int m = 0; m < 5; m++) sQ[m * NQ + e] = W[m * vs + Z];
+      }
+      const long long Z = Zc + (long long)(p + NG) * sz;
+      sC[t] = W[FLD_C * vs + Z];
+      sChi[t] = W[FLD_CHI * vs + Z];
+    }
+    __syncthreads();
+
+    // 2. trace plane p along x, y (from the staged plane) and z (column registers)
+    if (trace) {
+      const float cs = sC[t], f = sChi[t];
+      const int e0 = (cj + 3) * T::QX + (ci + 3);
+      const float rho = sQ[e0];
+      const float ic = nr_rcp(cs), cr = cs * nr_rcp(rho);
+      float a0[5], aL[5], aR[5];
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        const float* a = sQ + comp<0>(m) * NQ + e0;
+        a0[m] = a[0];
+        tile_parabola(a[-2], a[-1], a[0], a[1], a[2], f, aL[m], aR[m]);
+      }
+      trace_edges(a0, aL, aR, cs, ic, cr, dtdx[0], [&](int side, const float* out) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) tx_c[(side * 5 + m) * NR + t] = out[m];
+      });
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        const float* a = sQ + comp<1>(m) * NQ + e0;
+        a0[m] = a[0];
+        tile_parabola(a[-2 * T::QX], a[-T::QX], a[0], a[T::QX], a[2 * T::QX], f, aL[m], aR[m]);
+      }
+      trace_edges(a0, aL, aR, cs, ic, cr, dtdx[1], [&](int side, const float* out) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) ty_c[(side * 5 + m) * NR + t] = out[m];
+      });
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        const float d1 = vl_slope(q0[m], q1[m], q2[m]);
+        a0[m] = q0[m];
+        aL[m] = fl[m];
+        aR[m] = ppm_face(q0[m], q1[m], d0[m], d1);
+        fl[m] = aR[m];
+        cw84_limit(a0[m], f, aL[m], aR[m]);
+        d0[m] = d1;
+        q0[m] = q1[m];
+        q1[m] = q2[m];
+      }
+      trace_edges(a0, aL, aR, cs, ic, cr, dtdx[2], [&](int side, const float* out) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) tz_c[(side * 5 + m) * NR + t] = out[m];
+      });
+      if (p + 1 <= z1) {  // the plane three ahead, for the next plane's stencil
+        const long long Z = Zc + (long long)(p + 3 + NG) * sz;
+#pragma unroll
+        for (int m = 0; m < 5; m++) q2[m] = W[comp<2>(m) * vs + Z];
+      }
+    }
+    __syncthreads();
+
+    // 3. normal fluxes of plane p: x- and y-faces at the zone's low side, and
+    // the z-face between planes p-1 and p
+    if (trace) {
+      float qL[5], qR[5], uL[4], uR[4], Fn[5];
+      if (fc_x && in_y) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+          qL[m] = tx_c[(5 + m) * NR + t - 1];
+          qR[m] = tx_c[m * NR + t];
+        }
+        conserved_of(qL, igm1, uL);
+        conserved_of(qR, igm1, uR);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        tile_store<0>(f0x_c, NR, t, Fn);
+      }
+      if (fc_y && in_x) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+          qL[m] = ty_c[(5 + m) * NR + t - 32];
+          qR[m] = ty_c[m * NR + t];
+        }
+        conserved_of(qL, igm1, uL);
+        conserved_of(qR, igm1, uR);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        tile_store<1>(f0y_c, NR, t, Fn);
+      }
+      if (p >= z0 && in_x && in_y) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+          qL[m] = tz_p[(5 + m) * NR + t];
+          qR[m] = tz_c[m * NR + t];
+        }
+        conserved_of(qL, igm1, uL);
+        conserved_of(qR, igm1, uR);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        tile_store<2>(f0z_c, NR, t, Fn);
+      }
+    }
+    __syncthreads();
+
+    // 4. stage 1 through z-face p: F^{z|x} and F^{z|y}, from the left edge of
+    // plane p and the right edge of plane p-1, each corrected by the flux
+    // differences across its own zone
+    if (trace && p >= z0) {
+      float dl[1][5], Fn[5], qm[5], qpp[5];
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = tz_c[m * NR + t];
+        qpp[m] = tz_p[(5 + m) * NR + t];
+      }
+      if (int_x && in_y) {
+        const float fac[1] = {fac1[0]};
+        tile_delta<2>(f0x_c, NR, t, t + 1, dl[0]);
+        const EdgeF em = tile_correct1<1>(qm, dl, fac, gamma, igm1);
+        tile_delta<2>(f0x_p, NR, t, t + 1, dl[0]);
+        const EdgeF lp = tile_correct1<1>(qpp, dl, fac, gamma, igm1);
+        tile_flux<RS>(lp, em, gamma, igm1, Fn);
+        tile_store<2>(fzx_c, NR, t, Fn);
+      }
+      if (in_x && int_y) {
+        const float fac[1] = {fac1[1]};
+        tile_delta<2>(f0y_c, NR, t, t + 32, dl[0]);
+        const EdgeF em = tile_correct1<1>(qm, dl, fac, gamma, igm1);
+        tile_delta<2>(f0y_p, NR, t, t + 32, dl[0]);
+        const EdgeF lp = tile_correct1<1>(qpp, dl, fac, gamma, igm1);
+        tile_flux<RS>(lp, em, gamma, igm1, Fn);
+        tile_store<2>(fzy_c, NR, t, Fn);
+      }
+    }
+
+    // 5. stage 1 in plane p-1: x|y, x|z (x-faces, neighbours by shuffle),
+    // y|x, y|z (y-faces, neighbours through shared memory)
+    const int pm = p - 1;
+    if (p >= z0) {
+      const bool mid = pm >= z0 && pm < z1;
+      float dl[1][5], Fn[5], qm[5], qp[5];
+      EdgeF em, ep;
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = tx_p[m * NR + t];
+        qp[m] = tx_p[(5 + m) * NR + t];
+      }
+      {  // x|y
+        const float fac[1] = {fac1[1]};
+        tile_delta<0>(f0y_p, NR, t, t + 32, dl[0]);
+        tile_correct<1>(qm, qp, dl, fac, gamma, igm1, em, ep);
+        const EdgeF lp = shfl_up_edge(ep);
+        if (fc_x && int_y) {
+          tile_flux<RS>(lp, em, gamma, igm1, Fn);
+          tile_store<0>(sF1 + 0 * 5 * NR, NR, t, Fn);
+        }
+      }
+      if (mid) {  // x|z
+        const float fac[1] = {fac1[2]};
+#pragma unroll
+        for (int m = 0; m < 5; m++)
+          dl[0][m] = f0z_c[comp<0>(m) * NR + t] - f0z_p[comp<0>(m) * NR + t];
+        tile_correct<1>(qm, qp, dl, fac, gamma, igm1, em, ep);
+        const EdgeF lp = shfl_up_edge(ep);
+        if (fc_x && in_y) {
+          tile_flux<RS>(lp, em, gamma, igm1, Fn);
+          tile_store<0>(sF1 + 1 * 5 * NR, NR, t, Fn);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = ty_p[m * NR + t];
+        qp[m] = ty_p[(5 + m) * NR + t];
+      }
+      EdgeF ymx, ymz;
+      {  // y|x: corrected states; the right edge goes to the zone above
+        const float fac[1] = {fac1[0]};
+        tile_delta<1>(f0x_p, NR, t, t + 1, dl[0]);
+        tile_correct<1>(qm, qp, dl, fac, gamma, igm1, ymx, ep);
+        put_edge(ex0, NR, t, ep);
+      }
+      if (mid) {  // y|z
+        const float fac[1] = {fac1[2]};
+#pragma unroll
+        for (int m = 0; m < 5; m++)
+          dl[0][m] = f0z_c[comp<1>(m) * NR + t] - f0z_p[comp<1>(m) * NR + t];
+        tile_correct<1>(qm, qp, dl, fac, gamma, igm1, ymz, ep);
+        put_edge(ex1, NR, t, ep);
+      }
+      __syncthreads();
+      if (fc_y && int_x) {
+        const EdgeF lp = get_edge(ex0, NR, t - 32);
+        tile_flux<RS>(lp, ymx, gamma, igm1, Fn);
+        tile_store<1>(sF1 + 2 * 5 * NR, NR, t, Fn);
+      }
+      if (mid && fc_y && in_x) {
+        const EdgeF lp = get_edge(ex1, NR, t - 32);
+        tile_flux<RS>(lp, ymz, gamma, igm1, Fn);
+        tile_store<1>(sF1 + 3 * 5 * NR, NR, t, Fn);
+      }
+    }
+    __syncthreads();
+
+    // 6. stage 2 of plane p-1 along z: U^{z,fin}, and the final flux through
+    // its low z-face
+    float fz_new[5] = {0, 0, 0, 0, 0};
+    if (p >= z0 && int_x && int_y) {
+      float dl[2][5], qm[5], qp[5];
+      const float fac[2] = {0.5f * dtdx[0], 0.5f * dtdx[1]};
+      tile_delta<2>(sF1 + 0 * 5 * NR, NR, t, t + 1, dl[0]);
+      tile_delta<2>(sF1 + 2 * 5 * NR, NR, t, t + 32, dl[1]);
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = tz_p[m * NR + t];
+        qp[m] = tz_p[(5 + m) * NR + t];
+      }
+      EdgeF em, ep;
+      tile_correct<2>(qm, qp, dl, fac, gamma, igm1, em, ep);
+      if (pm >= z0) {
+        float Fn[5];
+        tile_flux<RS>(zfin, em, gamma, igm1, Fn);
+        tile_wall<2>(b, pm, Fn);
+#pragma unroll
+        for (int m = 0; m < 5; m++) fz_new[comp<2>(m)] = Fn[m];
+      }
+      zfin = ep;
+    }
+
+    // 7. FP64 update of plane p-2 (the order of update_zone)
+    if (upd) {
+      double nu[5];
+#pragma unroll
+      for (int v = 0; v < 5; v++) {
+        double val = uo[v];
+        val = val - dtdx64[0] * (widen(sFX[v * NR + t + 1]) - widen(sFX[v * NR + t]));
+        val = val - dtdx64[1] * (widen(sFY[v * NR + t + 32]) - widen(sFY[v * NR + t]));
+        val = val - dtdx64[2] * (widen(fz_new[v]) - widen(fz_prev[v]));
+        nu[v] = val;
+        U[v * vs + Zu] = val;
+      }
+      const double m2 = nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3];
+      const double e2 = 2.0 * nu[0] * nu[4] - m2;
+      if (!is_pos(nu[0]) || !is_pos(e2) || e2 != e2) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+    }
+    if (pm >= z0) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) fz_prev[v] = fz_new[v];
+    }
+    __syncthreads();
+
+    // 8. stage 2 of plane p-1 along x and y: the final fluxes through the
+    // zone's low x- and y-faces
+    if (pm >= z0 && pm < z1) {
+      float dl[2][5], Fn[5], qm[5], qp[5];
+      EdgeF em, ep;
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = tx_p[m * NR + t];
+        qp[m] = tx_p[(5 + m) * NR + t];
+      }
+      {
+        const float fac[2] = {0.5f * dtdx[1], 0.5f * dtdx[2]};
+        tile_delta<0>(sF1 + 3 * 5 * NR, NR, t, t + 32, dl[0]);
+#pragma unroll
+        for (int m = 0; m < 5; m++) dl[1][m] = fzy_c[comp<0>(m) * NR + t] - fzy_p[comp<0>(m) * NR + t];
+        tile_correct<2>(qm, qp, dl, fac, gamma, igm1, em, ep);
+        const EdgeF lp = shfl_up_edge(ep);
+        if (fc_x && int_y) {
+          tile_flux<RS>(lp, em, gamma, igm1, Fn);
+          tile_wall<0>(b, gx, Fn);
+          tile_store<0>(sFX, NR, t, Fn);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 5; m++) {
+        qm[m] = ty_p[m * NR + t];
+        qp[m] = ty_p[(5 + m) * NR + t];
+      }
+      {
+        const float fac[2] = {0.5f * dtdx[2], 0.5f * dtdx[0]};
+#pragma unroll
+        for (int m = 0; m < 5; m++) dl[0][m] = fzx_c[comp<1>(m) * NR + t] - fzx_p[comp<1>(m) * NR + t];
+        tile_delta<1>(sF1 + 1 * 5 * NR, NR, t, t + 1, dl[1]);
+        tile_correct<2>(qm, qp, dl, fac, gamma, igm1, em, ep);
+        put_edge(ex0, NR, t, ep);
+      }
+      __syncthreads();
+      if (fc_y && int_x) {
+        const EdgeF lp = get_edge(ex0, NR, t - 32);
+        tile_flux<RS>(lp, em, gamma, igm1, Fn);
+        tile_wall<1>(b, gy, Fn);
+        tile_store<1>(sFY, NR, t, Fn);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ----------------------------------------------------- host staging transfers
@@ -1847,11 +2391,11 @@ __global__ void __launch_bounds__(256) k_gather(TableView tv, const DevBox* __re
 }  // namespace
 
 const char* const STAGE_NAMES[NSTAGES] = {"fill_ghosts", "prim", "dt", "flatten", "slopes", "trace",
-                                           "riemann", "ctu1", "ctu2", "update"};
+                                           "riemann", "ctu1", "ctu2", "tile", "update"};
 
 const char* const TABLE_NAMES[NTABLES] = {"fill_x", "fill_y", "fill_z", "prim", "update", "flatten",
                                            "slopes", "trace", "riemann", "ctu1", "ctu2", "line_x", "line_yz",
-                                           "ctu2_line", "ctu1_line"};
+                                           "ctu2_line", "ctu1_line", "tile"};
 
 int default_tpb(int table) {
   switch (table) {
@@ -1919,6 +2463,10 @@ int build_table(const Plan& p, int table, int slot, int tpb, int order, int* sta
     if (!p.boxes[b].active) continue;
     const hydro_box_desc& d = p.boxes[b].d;
     if (TABLE_PER_PRECISION[table] && (d.precision == HYDRO_MIXED) != (slot == 1)) continue;
+    if (table == TB_TILE) {  // one block per tile and z-segment
+      items.push_back({b * 8, (int)tile_blocks(d, p.tile_ty, p.tile_seg)});
+      continue;
+    }
     for (int z = 0; z < TABLE_ZDIM[table]; z++) {
       const long long v = item_volume(d, table, z);
       items.push_back({b * 8 + z, (int)((v + tpb - 1) / tpb)});
@@ -2002,6 +2550,9 @@ int launch_typed(const Plan& p, int table, const WorkTable& w, cudaStream_t s) {
 // CTU stages for the face-wise ones.
 template <typename R>
 int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
+  if (tile_fused(p, slot) &&
+      (table == TB_SLOPES || table == TB_TRACE || table == TB_RIEMANN || table == TB_CTU1 || table == TB_CTU2))
+    return 0;
   if (line_fused(p, slot)) {
     if (table == TB_SLOPES || table == TB_RIEMANN) return 0;
     if (table == TB_TRACE)
@@ -2011,6 +2562,27 @@ int launch_slot(const Plan& p, int table, int slot, cudaStream_t s) {
     if (table == TB_CTU2) return launch_typed<R>(p, TB_CTU2_LINE, p.tab[TB_CTU2_LINE][slot], s);
   }
   return launch_typed<R>(p, table, p.tab[table][slot], s);
+}
+
+// The fused tile stage for FP32 boxes, if the plan runs it.
+template <int TY, int RS>
+int launch_tile_kernel(const Plan& p, const WorkTable& w, cudaStream_t s) {
+  if (w.nitems == 0) return 0;
+  const int seg = p.tile_seg > 0 ? p.tile_seg : (1 << 30);
+  k_tile<TY, RS><<<w.blocks, TileShape<TY>::NR, TileShape<TY>::BYTES, s>>>(view(w), p.dboxes, p.rt, p.state, p.work,
+                                                                          seg);
+  return 1;
+}
+
+int launch_tiles(const Plan& p, cudaStream_t s) {
+  if (!tile_fused(p, 1)) return 0;
+  const WorkTable& w = p.tab[TB_TILE][1];
+  const bool ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
+  if (p.tile_ty == TILE_TYS[0])
+    return ts ? launch_tile_kernel<TILE_TYS[0], HYDRO_RIEMANN_TWO_SHOCK>(p, w, s)
+              : launch_tile_kernel<TILE_TYS[0], HYDRO_RIEMANN_HLLC>(p, w, s);
+  return ts ? launch_tile_kernel<TILE_TYS[1], HYDRO_RIEMANN_TWO_SHOCK>(p, w, s)
+            : launch_tile_kernel<TILE_TYS[1], HYDRO_RIEMANN_HLLC>(p, w, s);
 }
 
 // Both compute types of a per-precision table.
@@ -2049,8 +2621,11 @@ cudaError_t launch_stage(const Plan& p, Stage st, cudaStream_t stream, const dou
     case ST_RIEMANN: n += launch_both(p, TB_RIEMANN, stream); break;
     case ST_CTU1: n += launch_both(p, TB_CTU1, stream); break;
     case ST_CTU2: n += launch_both(p, TB_CTU2, stream); break;
+    case ST_TILE:
+      n += launch_tiles(p, stream);
+      break;
     case ST_UPDATE:
-      n += launch(k_update, T[TB_UPDATE][0], stream, p.dboxes, p.rt, p.state, p.work);
+      n += launch(k_update, T[TB_UPDATE][0], stream, p.dboxes, p.rt, p.state, p.work, tile_fused(p, 1) ? 1 : 0);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -2082,10 +2657,32 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
       if (slot == 0) launch_typed<double>(p, table, w, stream);
       else launch_typed<float>(p, table, w, stream);
       break;
+    case TB_TILE:  // updates the state: the autotuner saves and restores it around this
+      launch_tiles(p, stream);
+      break;
     default:
       return cudaErrorInvalidValue;  // the update changes the state and is not relaunched
   }
   return cudaGetLastError();
+}
+
+cudaError_t prepare_tile_kernels() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaSuccess) return done;
+  cudaError_t e = cudaFuncSetAttribute(k_tile<TILE_TYS[0], HYDRO_RIEMANN_HLLC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TileShape<TILE_TYS[0]>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tile<TILE_TYS[0], HYDRO_RIEMANN_TWO_SHOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileShape<TILE_TYS[0]>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tile<TILE_TYS[1], HYDRO_RIEMANN_HLLC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileShape<TILE_TYS[1]>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tile<TILE_TYS[1], HYDRO_RIEMANN_TWO_SHOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileShape<TILE_TYS[1]>::BYTES);
+  done = e;
+  return e;
 }
 
 cudaError_t launch_scatter(const Plan& p, const double* stage, cudaStream_t stream) {

@@ -20,25 +20,30 @@ struct PrimZone {
 
 __device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, double mz, double E,
                                               double gamma) {
+  // every operation written out with its rounding (fused where the product
+  // feeds a sum), so that no kernel that inlines this can contract it
+  // differently from another
   PrimZone z;
   if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
   z.rho = rho;
   z.ir = nr_rcp(rho);
-  z.u = mx * z.ir;
-  z.v = my * z.ir;
-  z.w = mz * z.ir;
-  double p = (gamma - 1.0) * (E - 0.5 * rho * (z.u * z.u + z.v * z.v + z.w * z.w));
+  z.u = __dmul_rn(mx, z.ir);
+  z.v = __dmul_rn(my, z.ir);
+  z.w = __dmul_rn(mz, z.ir);
+  const double uu = __fma_rn(z.w, z.w, __fma_rn(z.v, z.v, __dmul_rn(z.u, z.u)));
+  double p = __dmul_rn(__dsub_rn(gamma, 1.0), __fma_rn(__dmul_rn(-0.5, rho), uu, E));
   if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
   z.p = p;
-  const double c2 = gamma * p * z.ir;
+  const double c2 = __dmul_rn(__dmul_rn(gamma, p), z.ir);
   z.ic = nr_rsqrt(c2);
-  z.cs = c2 * z.ic;
+  z.cs = __dmul_rn(c2, z.ic);
   return z;
 }
 
 // max over the axes d of (|u_d| + c) / dx_d, given idx[d] = 1 / dx_d
 __device__ __forceinline__ double signal_rate(double u, double v, double w, double cs, const double* idx) {
-  return dmax(dmax((fabs(u) + cs) * idx[0], (fabs(v) + cs) * idx[1]), (fabs(w) + cs) * idx[2]);
+  return dmax(dmax(__dmul_rn(__dadd_rn(fabs(u), cs), idx[0]), __dmul_rn(__dadd_rn(fabs(v), cs), idx[1])),
+              __dmul_rn(__dadd_rn(fabs(w), cs), idx[2]));
 }
 
 }  // namespace hydro

@@ -37,7 +37,8 @@ EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_fr
             "hydro_profile_end", "hydro_compute_dt_noalloc", "hydro_autotune", "hydro_use_graphs",
             "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
             "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_set_method",
-            "hydro_fuse_lines", "hydro_last_error")
+            "hydro_fuse_lines", "hydro_fuse_tiles", "hydro_set_tile_shape", "hydro_measure_peaks",
+            "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -60,7 +61,8 @@ class hydro_layout(ctypes.Structure):
 
 class hydro_tuning(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("precision", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("order", ctypes.c_int32), ("ms", ctypes.c_float), ("tile_rows", ctypes.c_int32),
+                ("tile_seg", ctypes.c_int32)]
 
 
 class hydro_server_config(ctypes.Structure):
@@ -121,9 +123,13 @@ def load(path: str | None = None):
         L.hydro_profile_begin.argtypes = [_VP]
         L.hydro_profile_end.argtypes = [_VP, ctypes.POINTER(hydro_stage_time), i, ctypes.POINTER(i)]
         L.hydro_compute_dt_noalloc.argtypes = [D, i, _VP, _VP, _VP]
+        L.hydro_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(i), _VP]
         L.hydro_autotune.argtypes = [_VP, i, ctypes.POINTER(hydro_tuning), i, ctypes.POINTER(i), _VP]
         L.hydro_use_graphs.argtypes = [_VP, i]
         L.hydro_fuse_lines.argtypes = [_VP, i]
+        L.hydro_fuse_tiles.argtypes = [_VP, i]
+        L.hydro_set_tile_shape.argtypes = [_VP, i, i]
         L.hydro_set_neighbors.argtypes = [_VP, _VP]
         L.hydro_set_shared_dt.argtypes = [_VP, i]
         L.hydro_set_method.argtypes = [_VP, i, i]
@@ -274,11 +280,12 @@ def hydro_profile_end(h: int) -> dict:
 
 
 def hydro_autotune(h: int, reps: int = 3, stream=None) -> list:
-    """[(table, precision, threads, order, ms)] chosen per stage table."""
+    """[(table, precision, threads, order, ms, tile rows, tile segment)] chosen per stage table."""
     buf = (hydro_tuning * 64)()
     n = ctypes.c_int()
     _check(load().hydro_autotune(h, int(reps), buf, 64, ctypes.byref(n), _stream(stream)))
-    return [(buf[k].name.decode(), buf[k].precision, buf[k].threads, buf[k].order, buf[k].ms) for k in range(n.value)]
+    return [(buf[k].name.decode(), buf[k].precision, buf[k].threads, buf[k].order, buf[k].ms, buf[k].tile_rows,
+             buf[k].tile_seg) for k in range(n.value)]
 
 
 def hydro_set_neighbors(h: int, neighbors) -> None:
@@ -296,6 +303,15 @@ def hydro_set_method(h: int, limiter: int = 0, riemann: int = 0) -> None:
     _check(load().hydro_set_method(h, int(limiter), int(riemann)))
 
 
+def hydro_fuse_tiles(h: int, enable: bool) -> None:
+    _check(load().hydro_fuse_tiles(h, int(bool(enable))))
+
+
+def hydro_set_tile_shape(h: int, rows: int, seg: int) -> None:
+    """Tile rows (2 or 6) and z-planes per segment (0: the whole box) of the fused tile stage."""
+    _check(load().hydro_set_tile_shape(h, int(rows), int(seg)))
+
+
 def hydro_use_graphs(h: int, enable: bool) -> None:
     _check(load().hydro_use_graphs(h, int(bool(enable))))
 
@@ -309,6 +325,13 @@ def hydro_compute_dt_noalloc(descs, state_dev, dt_dev, stream=None) -> None:
     without a handle or caller scratch (the library's static scratch is used)."""
     _check(load().hydro_compute_dt_noalloc(desc_array(descs), len(descs), _ptr(state_dev), _ptr(dt_dev),
                                            _stream(stream)))
+
+
+def hydro_measure_peaks(stream=None) -> dict:
+    """Measured FP64 and FP32 multiply-add rates (flop/s) and the SM count."""
+    f64, f32, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(load().hydro_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(sms), _stream(stream)))
+    return {"fp64_flops": f64.value, "fp32_flops": f32.value, "sms": sms.value}
 
 
 def hydro_server_create(pool_dev, pool_bytes: int, max_active: int, dry_run: bool = False) -> int:
