@@ -266,6 +266,27 @@ int hydro_fuse_lines(hydro_handle* h, int enable);
 int hydro_fuse_tiles(hydro_handle* h, int enable);
 int hydro_set_tile_shape(hydro_handle* h, int rows, int seg);
 
+/* Persistent form.  hydro_persistent(h, 1) makes hydro_step advance every box
+ * by all nsteps steps in one launch of one kernel: its blocks (as many as fit
+ * on the GPU at once) take work blocks of the stage tables from a queue in
+ * step, stage and box order, and a work block of a box's stage first waits
+ * until the box's blocks of every earlier stage (of this and earlier steps)
+ * are done.  Small or uneven boxes then flow through the stages without a
+ * device-wide barrier between stages.  Every wait polls a bounded number of
+ * times (hydro_set_spin_limit; about half a second by default): when one gives
+ * up, the launch stops taking work and the next hydro_sync returns
+ * HYDRO_ERR_TIMEOUT (the step it interrupted is incomplete).  The stage work
+ * is the per-stage form's own code, so results are bitwise the same.  Needs
+ * independent boxes (no hydro_set_neighbors links, no shared dt) and the fused
+ * tile stage off; every stage table is rebuilt for 128-thread blocks, so
+ * hydro_autotune is refused while the form is on.  Stage times are not
+ * recorded by hydro_profile_* in this form.
+ * hydro_set_spin_limit sets the polls before a wait gives up; stall_box >= 0
+ * makes one wait of that box's second stage unreachable, which exercises the
+ * give-up path (tests); -1 for normal operation. */
+int hydro_persistent(hydro_handle* h, int enable);
+int hydro_set_spin_limit(hydro_handle* h, int64_t polls, int stall_box);
+
 /* Number of kernels this handle has launched since hydro_alloc (a ghost fill
  * is three kernels, every other stage one per compute type present), into
  * *count. */

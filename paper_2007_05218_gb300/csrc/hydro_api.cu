@@ -75,7 +75,7 @@ int validate(const hydro_box_desc& d, int i) {
 struct Geometry {
   std::vector<HostBox> boxes;
   size_t state_elems = 0;
-  size_t table_bytes = 0, rt_bytes = 0, worktab_bytes = 0, head_bytes = 0;
+  size_t table_bytes = 0, rt_bytes = 0, worktab_bytes = 0, persist_bytes = 0, head_bytes = 0;
   int cap[hydro::NTABLES][2] = {};  // work-table capacities (items)
   size_t work_bytes = 0, stage_elems = 0;
   size_t scratch_bytes = 0;
@@ -123,7 +123,13 @@ int plan_geometry(const hydro_box_desc* d, int nboxes, Geometry* g) {
       if (g->cap[t][s]) ints += 2 * (size_t)g->cap[t][s] + 1;
   }
   g->worktab_bytes = align_up(ints * sizeof(int), ALIGN);
-  g->head_bytes = g->table_bytes + g->rt_bytes + g->worktab_bytes;
+  // persistent form: queue and error word, done counts, per-stage block
+  // counts, and the work table of the per-box dt stage
+  g->persist_bytes = align_up(sizeof(hydro::PersistHead), ALIGN) +
+                     align_up(sizeof(unsigned long long) * nboxes, ALIGN) +
+                     align_up(sizeof(long long) * (size_t)nboxes * (hydro::NPSTAGES + 1), ALIGN) +
+                     align_up(sizeof(int) * (2 * (size_t)nboxes + 1), ALIGN);
+  g->head_bytes = g->table_bytes + g->rt_bytes + g->worktab_bytes + g->persist_bytes;
   // the field area doubles as the staging buffer of hydro_upload/download
   g->scratch_bytes = g->head_bytes + std::max(g->work_bytes, g->stage_elems * sizeof(double));
   return HYDRO_OK;
@@ -159,6 +165,9 @@ cudaError_t upload_table(hydro_handle* h, int t, int s) {
   drop_graph(h);
   return e;
 }
+
+// Rebuilds the tables of the persistent form (defined with hydro_persistent).
+cudaError_t setup_persistent(hydro_handle* h, bool on);
 
 // Launches one stage, bracketed by timing events when profiling is on.
 cudaError_t run_stage(hydro_handle* h, hydro::Stage st, cudaStream_t s, const double* dt_in = nullptr,
@@ -246,6 +255,64 @@ int ensure_graph(hydro_handle* h, const double* dt_dev) {
   }
   h->graph_dt = dt_dev;
   return HYDRO_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Rebuilds every stage table for the persistent block size (or back to each
+// table's default), the dt stage's table and the per-box block counts of
+// each persistent stage.
+cudaError_t setup_persistent(hydro_handle* h, bool on) {
+  hydro::Plan& p = h->plan;
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < hydro::NTABLES && e == cudaSuccess; t++)
+    for (int sl = 0; sl < 2 && e == cudaSuccess; sl++) {
+      if (t == hydro::TB_TILE) continue;
+      p.tab[t][sl].tpb = on ? hydro::PERSIST_THREADS : hydro::default_tpb(t);
+      e = upload_table(h, t, sl);
+    }
+  if (e != cudaSuccess || !on) return e;
+  const int n = p.nboxes;
+  std::vector<long long> need((size_t)n * (hydro::NPSTAGES + 1), 0);
+  for (int st = 0; st < hydro::NPSTAGES; st++) {
+    int t, sl;
+    hydro::persist_stage_table(st, &t, &sl);
+    std::vector<long long> cnt(n, 0);
+    if (t < 0) {
+      for (int b = 0; b < n; b++) cnt[b] = h->boxes[b].active ? 1 : 0;
+    } else if (hydro::persist_stage_runs(p, st)) {
+      const hydro::WorkTable& w = p.tab[t][sl];
+      std::vector<int> start(w.capacity + 1), item(w.capacity);
+      const int ni = w.capacity ? hydro::build_table(p, t, sl, w.tpb, w.order, start.data(), item.data()) : 0;
+      for (int i = 0; i < ni; i++) cnt[item[i] >> 3] += start[i + 1] - start[i];
+    }
+    for (int b = 0; b < n; b++) {
+      long long* nb = need.data() + (size_t)b * (hydro::NPSTAGES + 1);
+      if (st + 1 <= hydro::NPSTAGES) nb[st + 1] = nb[st] + cnt[b];
+    }
+  }
+  // need[b][st]: blocks of box b in the stages before st; need[b][NPSTAGES]:
+  // its blocks per step
+  std::vector<int> dts(n + 1), dti(n);
+  int k = 0;
+  for (int b = 0; b < n; b++) {
+    if (!h->boxes[b].active) continue;
+    dts[k] = k;
+    dti[k] = b * 8;
+    k++;
+  }
+  dts[k] = k;
+  p.p_dt_items = k;
+  e = cudaMemcpy(p.p_need, need.data(), sizeof(long long) * need.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p.p_dt_start, dts.data(), sizeof(int) * (k + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && k) e = cudaMemcpy(p.p_dt_item, dti.data(), sizeof(int) * k, cudaMemcpyHostToDevice);
+  int occ = 0, sms = 0;
+  if (e == cudaSuccess) e = hydro::persist_occupancy(p, &occ);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  p.persist_grid = std::max(1, occ) * std::max(1, sms);
+  return e;
 }
 
 }  // namespace
@@ -338,6 +405,17 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
         }
       }
   }
+  {
+    char* pp = scratch + g.table_bytes + g.rt_bytes + g.worktab_bytes;
+    p.p_head = reinterpret_cast<hydro::PersistHead*>(pp);
+    pp += align_up(sizeof(hydro::PersistHead), ALIGN);
+    p.p_done = reinterpret_cast<unsigned long long*>(pp);
+    pp += align_up(sizeof(unsigned long long) * nboxes, ALIGN);
+    p.p_need = reinterpret_cast<long long*>(pp);
+    pp += align_up(sizeof(long long) * (size_t)nboxes * (hydro::NPSTAGES + 1), ALIGN);
+    p.p_dt_start = reinterpret_cast<int*>(pp);
+    p.p_dt_item = p.p_dt_start + nboxes + 1;
+  }
   p.state = static_cast<double*>(state_dev);
   p.work = reinterpret_cast<unsigned char*>(scratch + g.head_bytes);
   p.work_bytes = g.work_bytes;
@@ -383,6 +461,7 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
   h->dbox_host = table;
   e = cudaMemcpy(p.dboxes, table.data(), sizeof(DevBox) * nboxes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p.rt, 0, sizeof(BoxRt) * nboxes);
+  if (e == cudaSuccess) e = cudaMemset(p.p_head, 0, sizeof(hydro::PersistHead));
   for (int t = 0; t < hydro::NTABLES && e == cudaSuccess; t++)
     for (int s = 0; s < 2 && e == cudaSuccess; s++) e = upload_table(h, t, s);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -427,6 +506,15 @@ int hydro_step(hydro_handle* h, const double* dt_dev, int nsteps, void* stream) 
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (nsteps == 0) return HYDRO_OK;
+  if (h->plan.persistent) {
+    // one launch for all nsteps steps; the queue and the done counts start at zero
+    cudaError_t e = cudaMemsetAsync(&h->plan.p_head->queue, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->plan.p_done, 0, sizeof(unsigned long long) * h->plan.nboxes, s);
+    if (e == cudaSuccess) e = hydro::launch_persistent(h->plan, dt_dev, nsteps, s);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent step launch");
+    h->launches += 1;
+    return HYDRO_OK;
+  }
   if (h->use_graphs && !h->profiling) {
     rc = ensure_graph(h, dt_dev);
     if (rc) return rc;
@@ -451,6 +539,22 @@ int hydro_sync(hydro_handle* h, void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "hydro_sync");
   const int n = h->plan.nboxes;
+  hydro::PersistHead ph;
+  e = cudaMemcpy(&ph, h->plan.p_head, sizeof ph, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "hydro_sync: reading the persistent status");
+  if (ph.err != 0) {
+    // clear the error word and the signal-speed maxima the interrupted step
+    // may have left, so that the next step starts clean
+    e = cudaMemset(&h->plan.p_head->err, 0, sizeof(int));
+    std::vector<BoxRt> rt0(n);
+    if (e == cudaSuccess) e = cudaMemcpy(rt0.data(), h->plan.rt, sizeof(BoxRt) * n, cudaMemcpyDeviceToHost);
+    for (BoxRt& r : rt0) r.smax = 0ull;
+    if (e == cudaSuccess) e = cudaMemcpy(h->plan.rt, rt0.data(), sizeof(BoxRt) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "hydro_sync: clearing the persistent status");
+    return fail(HYDRO_ERR_TIMEOUT,
+                "persistent step: a block waited longer than the spin limit for the blocks of an earlier stage of "
+                "its box and the launch gave up (the state of that step is incomplete)");
+  }
   std::vector<BoxRt> rt(n);
   e = cudaMemcpy(rt.data(), h->plan.rt, sizeof(BoxRt) * n, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "hydro_sync: reading status");
@@ -519,6 +623,7 @@ int hydro_download(hydro_handle* h, double* state_host, size_t bytes, void* stre
 
 int hydro_set_neighbors(hydro_handle* h, const int32_t* neighbors) {
   if (!h || !neighbors) return fail(HYDRO_ERR_INVALID, "null argument");
+  if (h->plan.persistent) return fail(HYDRO_ERR_INVALID, "hydro_set_neighbors: switch the persistent form off first");
   int rc = check_device(h);
   if (rc) return rc;
   const int n = h->plan.nboxes;
@@ -555,6 +660,8 @@ int hydro_set_neighbors(hydro_handle* h, const int32_t* neighbors) {
 
 int hydro_set_shared_dt(hydro_handle* h, int enable) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  if (enable && h->plan.persistent)
+    return fail(HYDRO_ERR_INVALID, "hydro_set_shared_dt: switch the persistent form off first");
   h->plan.shared_dt = enable != 0;
   drop_graph(h);
   return HYDRO_OK;
@@ -569,6 +676,7 @@ int hydro_set_method(hydro_handle* h, int limiter, int riemann) {
   h->plan.limiter = limiter;
   h->plan.riemann = riemann;
   drop_graph(h);
+  if (h->plan.persistent) return launched(setup_persistent(h, true), "hydro_set_method");
   return HYDRO_OK;
 }
 
@@ -576,6 +684,33 @@ int hydro_fuse_lines(hydro_handle* h, int enable) {
   if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
   h->plan.fuse_lines = enable != 0;
   drop_graph(h);
+  if (h->plan.persistent) return launched(setup_persistent(h, true), "hydro_fuse_lines");
+  return HYDRO_OK;
+}
+
+
+int hydro_persistent(hydro_handle* h, int enable) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  int rc = check_device(h);
+  if (rc) return rc;
+  hydro::Plan& p = h->plan;
+  if (enable) {
+    if (p.fuse_tiles) return fail(HYDRO_ERR_INVALID, "hydro_persistent: switch the fused tile stage off first");
+    if (p.shared_dt) return fail(HYDRO_ERR_INVALID, "hydro_persistent: boxes with a shared dt are not independent");
+    for (const DevBox& db : h->dbox_host)
+      for (int f = 0; f < 6; f++)
+        if (db.nbr1[f]) return fail(HYDRO_ERR_INVALID, "hydro_persistent: linked boxes are not independent");
+  }
+  p.persistent = enable != 0;
+  return launched(setup_persistent(h, p.persistent), "hydro_persistent");
+}
+
+int hydro_set_spin_limit(hydro_handle* h, int64_t polls, int stall_box) {
+  if (!h) return fail(HYDRO_ERR_INVALID, "null handle");
+  if (polls < 0) return fail(HYDRO_ERR_INVALID, "hydro_set_spin_limit: polls must be >= 0");
+  if (stall_box < -1 || stall_box >= h->plan.nboxes) return fail(HYDRO_ERR_INVALID, "hydro_set_spin_limit: bad box");
+  h->plan.spin_limit = polls;
+  h->plan.stall_box = stall_box;
   return HYDRO_OK;
 }
 
@@ -584,6 +719,7 @@ int hydro_fuse_tiles(hydro_handle* h, int enable) {
   int rc = check_device(h);
   if (rc) return rc;
   if (enable) {
+    if (h->plan.persistent) return fail(HYDRO_ERR_INVALID, "hydro_fuse_tiles: switch the persistent form off first");
     cudaError_t e = hydro::prepare_tile_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "hydro_fuse_tiles");
   }
@@ -697,6 +833,9 @@ int hydro_autotune(hydro_handle* h, int reps, hydro_tuning* out, int max_entries
   if (reps < 1) return fail(HYDRO_ERR_INVALID, "reps must be >= 1");
   int rc = check_device(h);
   if (rc) return rc;
+  if (h->plan.persistent)
+    return fail(HYDRO_ERR_INVALID, "hydro_autotune: the persistent form fixes the block size; tune before switching "
+                                   "it on");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   hydro::Plan& p = h->plan;
   // scratch in a consistent state for the current interior, time not advanced

