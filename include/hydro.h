@@ -49,7 +49,7 @@ extern "C" {
 #define HYDRO_ERR_INVALID (-1)     /* bad argument or descriptor */
 #define HYDRO_ERR_NOMEM (-2)       /* buffer too small or over the memory budget */
 #define HYDRO_ERR_NONPHYSICAL (-3) /* rho <= 0, p <= 0 or NaN after an update */
-#define HYDRO_ERR_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define HYDRO_ERR_TIMEOUT (-4)     /* a bounded device wait of the persistent form gave up */
 #define HYDRO_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 
 /* ---- boundary conditions (one per box face) ---- */
@@ -101,10 +101,16 @@ int hydro_workspace_size(const hydro_box_desc* d, int nboxes, size_t* state_byte
 int hydro_box_layout(const hydro_box_desc* d, int nboxes, int box, hydro_layout* out);
 
 /* Creates a handle over caller-owned device buffers of at least the sizes
- * given by hydro_workspace_size.  state_dev and scratch_dev must be 256-byte
- * aligned and stay valid until hydro_free.  Copies the box table into the
- * head of scratch_dev (synchronously) and zeroes the per-box time, dt and
- * status.  The state contents are left alone.  *out receives the handle. */
+ * given by hydro_workspace_size.  Source: the paper's boxes of data ("Fabs")
+ * with lo/hi bounds and several components (§2, Fig. 1), kept resident on the
+ * GPU for the whole run (§3, memory management).  state_dev and scratch_dev
+ * must be 256-byte aligned and stay valid until hydro_free (the library
+ * borrows them and never frees them).  Copies the box table into the head of
+ * scratch_dev (synchronously) and zeroes the per-box time, dt and status.  The
+ * state contents are left alone.  *out receives the handle.  Errors:
+ * HYDRO_ERR_INVALID (bad descriptor, null or misaligned buffer; *out stays
+ * NULL), HYDRO_ERR_NOMEM (a buffer smaller than hydro_workspace_size asks),
+ * HYDRO_ERR_CUDA. */
 int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t state_bytes,
                 void* scratch_dev, size_t scratch_bytes, hydro_handle** out);
 
@@ -112,23 +118,40 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
 int hydro_free(hydro_handle* h);
 
 /* Fills the ghost zones of every box from its boundary conditions, in the
- * order x, then y, then z, so that edges and corners are filled too. */
+ * order x, then y, then z, so that edges and corners are filled too.  Source:
+ * the ghost cells around each box's lo/hi interior that the stencil reads
+ * (§2, Fig. 1; §3).  Asynchronous on `stream`; HYDRO_ERR_INVALID for a null
+ * handle or one used on another device, HYDRO_ERR_CUDA on a launch failure. */
 int hydro_fill_ghosts(hydro_handle* h, void* stream);
 
 /* Computes each box's CFL time step from its current interior state,
- * dt_b = cfl * min over zones and axes of dx_a / (|u_a| + c), into
- * dt_dev[0..nboxes-1] (device memory, written asynchronously). */
+ * dt_b = cfl / max over zones and axes of (|u_a| + c) / dx_a (the CFL step
+ * cfl * min dx_a / (|u_a| + c)), into dt_dev[0..nboxes-1] (device memory,
+ * caller-owned, written asynchronously).  Source: the time step set by the
+ * zone width and the signal speed, which makes the paper's throughput a count
+ * of zones per time step (§4).  The ghost zones must be filled (the
+ * primitive conversion runs over the ghosted box).  Errors as for
+ * hydro_fill_ghosts. */
 int hydro_compute_dt(hydro_handle* h, double* dt_dev, void* stream);
 
 /* Advances every box by `nsteps` steps.  Each step fills the ghost zones,
  * takes dt from dt_dev[b] (or, if dt_dev is NULL, computes it from the state
  * as hydro_compute_dt does) and applies one unsplit PPM/CTU/HLLC update to the
- * interior.  nsteps == 0 does nothing.  Asynchronous on `stream`. */
+ * interior.  Source: the hydro update of §3 (limited slopes from neighbouring
+ * zones, a reconstructed polynomial, fluxes, the state update), applied to
+ * every zone of every box per step as the paper's zones-per-time-step
+ * throughput counts it (§4).  nsteps == 0 does nothing.  Asynchronous on
+ * `stream`; device-side errors (a nonphysical state, a persistent-form
+ * timeout) are reported by the next hydro_sync.  HYDRO_ERR_INVALID for a null
+ * handle or nsteps < 0, HYDRO_ERR_CUDA on a launch failure. */
 int hydro_step(hydro_handle* h, const double* dt_dev, int nsteps, void* stream);
 
-/* Waits for `stream`, then reports the first device-side error of any box:
- * HYDRO_ERR_NONPHYSICAL if an update produced rho <= 0, p <= 0 or NaN.  The
- * error flags are cleared after being reported. */
+/* Waits for `stream`, then reports the first device-side error:
+ * HYDRO_ERR_TIMEOUT if a wait of the persistent form gave up (the interrupted
+ * step is incomplete; the per-box signal-speed maxima are cleared so that the
+ * next step starts clean), else HYDRO_ERR_NONPHYSICAL if an update produced
+ * rho <= 0, p <= 0 or NaN in some box.  The error flags are cleared after
+ * being reported. */
 int hydro_sync(hydro_handle* h, void* stream);
 
 /* Simulated time advanced so far by each box, into time_host[0..nboxes-1]
@@ -350,6 +373,9 @@ int hydro_compute_dt_noalloc(const hydro_box_desc* d, int nboxes, const double* 
                              void* stream);
 
 /* ---- served form: continuous batching of independent requests ----
+ * Source: data kept resident on the GPU and scratch served from a caching
+ * pool (§3, memory management), and several independent boxes in flight at
+ * once to keep the GPU busy (§4.A); each request is one box of §2.
  * A server owns one scheduler thread and a caller-owned device pool (the
  * memory budget).  hydro_submit copies a request (box, interior initial state,
  * step count) and returns at once with a ticket.  The scheduler admits queued
@@ -395,6 +421,9 @@ int hydro_server_create(const hydro_server_config* cfg, hydro_server** out);
 /* Stops admitting (queued requests are cancelled with HYDRO_ERR_INVALID),
  * finishes the resident ones, joins the scheduler and releases host state. */
 int hydro_server_destroy(hydro_server* s);
+/* Queues a request (its initial state is copied before the call returns) and
+ * writes its ticket.  HYDRO_ERR_INVALID for a bad descriptor or step count,
+ * HYDRO_ERR_NOMEM when the request could never fit the pool. */
 int hydro_submit(hydro_server* s, const hydro_request* r, int64_t* ticket);
 /* HYDRO_PENDING while running; HYDRO_OK once done (copies the interior result,
  * [5][nz][ny][nx] doubles, into out_host when it is not NULL; out_bytes must

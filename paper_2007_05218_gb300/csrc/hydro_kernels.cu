@@ -2564,7 +2564,9 @@ __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
   return v;
 }
 
-template <int LIM, int RS>
+// SLOTS: which compute types the handle holds (1 FP64, 2 FP32, 3 both); a
+// kernel that calls only one type's stage bodies needs fewer registers.
+template <int LIM, int RS, int SLOTS>
 __global__ void __launch_bounds__(PERSIST_THREADS) k_persist(const __grid_constant__ PersistArgs a) {
   __shared__ long long s_base;
   __shared__ int s_stage, s_box, s_blk, s_item, s_ok;
@@ -2631,6 +2633,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS) k_persist(const __grid_consta
       const int st = s_stage, bx = s_box, vb = s_blk;
       // a one-item view of the table: the body's own search is then trivial
       const TableView tv{a.tv[st].start + s_item, a.tv[st].item + s_item, 1};
+      constexpr bool D = (SLOTS & 1) != 0, F = (SLOTS & 2) != 0;
       switch (st) {
         case PS_FILL_X: b_fill<0>(tv, vb, a.boxes, a.state); break;
         case PS_FILL_Y: b_fill<1>(tv, vb, a.boxes, a.state); break;
@@ -2639,22 +2642,22 @@ __global__ void __launch_bounds__(PERSIST_THREADS) k_persist(const __grid_consta
         case PS_DT:
           if (threadIdx.x == 0) b_dt_box(a.boxes, a.rt, bx, a.dt_in, nullptr, 1);
           break;
-        case PS_FLATTEN_D: b_flatten<double>(tv, vb, a.boxes, a.work); break;
-        case PS_FLATTEN_F: b_flatten<float>(tv, vb, a.boxes, a.work); break;
-        case PS_SLOPES_D: b_slopes<double, LIM>(tv, vb, a.boxes, a.work); break;
-        case PS_SLOPES_F: b_slopes<float, LIM>(tv, vb, a.boxes, a.work); break;
-        case PS_TRACE_D: b_trace<double, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_TRACE_F: b_trace<float, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_LINE_X: b_line_x<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_LINE_YZ: b_line_yz<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_RIEMANN_D: b_riemann<double, RS>(tv, vb, a.boxes, a.work); break;
-        case PS_RIEMANN_F: b_riemann<float, RS>(tv, vb, a.boxes, a.work); break;
-        case PS_CTU1_D: b_ctu1<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_CTU1_F: b_ctu1<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_CTU1_LINE: b_ctu1_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_CTU2_D: b_ctu2<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_CTU2_F: b_ctu2<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
-        case PS_CTU2_LINE: b_ctu2_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_FLATTEN_D: if constexpr (D) b_flatten<double>(tv, vb, a.boxes, a.work); break;
+        case PS_FLATTEN_F: if constexpr (F) b_flatten<float>(tv, vb, a.boxes, a.work); break;
+        case PS_SLOPES_D: if constexpr (D) b_slopes<double, LIM>(tv, vb, a.boxes, a.work); break;
+        case PS_SLOPES_F: if constexpr (F) b_slopes<float, LIM>(tv, vb, a.boxes, a.work); break;
+        case PS_TRACE_D: if constexpr (D) b_trace<double, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_TRACE_F: if constexpr (F) b_trace<float, LIM>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_LINE_X: if constexpr (F) b_line_x<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_LINE_YZ: if constexpr (F) b_line_yz<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_RIEMANN_D: if constexpr (D) b_riemann<double, RS>(tv, vb, a.boxes, a.work); break;
+        case PS_RIEMANN_F: if constexpr (F) b_riemann<float, RS>(tv, vb, a.boxes, a.work); break;
+        case PS_CTU1_D: if constexpr (D) b_ctu1<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU1_F: if constexpr (F) b_ctu1<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU1_LINE: if constexpr (F) b_ctu1_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_D: if constexpr (D) b_ctu2<double, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_F: if constexpr (F) b_ctu2<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
+        case PS_CTU2_LINE: if constexpr (F) b_ctu2_line<float, RS>(tv, vb, a.boxes, a.rt, a.work); break;
         default: b_update(tv, vb, a.boxes, a.rt, a.state, a.work, 0); break;
       }
       __syncthreads();
@@ -2991,18 +2994,26 @@ bool persist_stage_runs(const Plan& p, int st) {
 }
 
 namespace {
+// The persistent kernel for the plan's method and compute types.
 template <int LIM, int RS>
-cudaError_t persist_occ(int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_persist<LIM, RS>, PERSIST_THREADS, 0);
+void (*persist_kernel_m(int slots))(PersistArgs) {
+  if (slots == 1) return k_persist<LIM, RS, 1>;
+  if (slots == 2) return k_persist<LIM, RS, 2>;
+  return k_persist<LIM, RS, 3>;
+}
+
+void (*persist_kernel(const Plan& p))(PersistArgs) {
+  const int slots = (p.has_fp64 ? 1 : 0) | (p.has_mixed ? 2 : 0);
+  const bool cs = p.limiter == HYDRO_LIMITER_CS08, ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
+  if (cs) return ts ? persist_kernel_m<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_TWO_SHOCK>(slots)
+                    : persist_kernel_m<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_HLLC>(slots);
+  return ts ? persist_kernel_m<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_TWO_SHOCK>(slots)
+            : persist_kernel_m<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_HLLC>(slots);
 }
 }  // namespace
 
 cudaError_t persist_occupancy(const Plan& p, int* n) {
-  const bool cs = p.limiter == HYDRO_LIMITER_CS08, ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
-  if (cs) return ts ? persist_occ<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_TWO_SHOCK>(n)
-                    : persist_occ<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_HLLC>(n);
-  return ts ? persist_occ<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_TWO_SHOCK>(n)
-            : persist_occ<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_HLLC>(n);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, persist_kernel(p), PERSIST_THREADS, 0);
 }
 
 cudaError_t launch_persistent(const Plan& p, const double* dt_in, int nsteps, cudaStream_t stream) {
@@ -3035,15 +3046,7 @@ cudaError_t launch_persistent(const Plan& p, const double* dt_in, int nsteps, cu
   a.nsteps = nsteps;
   a.spin_limit = p.spin_limit;
   a.stall_box = p.stall_box;
-  const bool cs = p.limiter == HYDRO_LIMITER_CS08, ts = p.riemann == HYDRO_RIEMANN_TWO_SHOCK;
-  const dim3 grid(p.persist_grid), block(PERSIST_THREADS);
-  if (cs) {
-    if (ts) k_persist<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_TWO_SHOCK><<<grid, block, 0, stream>>>(a);
-    else k_persist<HYDRO_LIMITER_CS08, HYDRO_RIEMANN_HLLC><<<grid, block, 0, stream>>>(a);
-  } else {
-    if (ts) k_persist<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_TWO_SHOCK><<<grid, block, 0, stream>>>(a);
-    else k_persist<HYDRO_LIMITER_CW84, HYDRO_RIEMANN_HLLC><<<grid, block, 0, stream>>>(a);
-  }
+  persist_kernel(p)<<<dim3(p.persist_grid), dim3(PERSIST_THREADS), 0, stream>>>(a);
   return cudaGetLastError();
 }
 
