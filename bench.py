@@ -64,7 +64,7 @@ FLOPS_PER_UNIT = {
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
 # stands; a stage missing here has no capture of its current code and reports
 # traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.554235e9 + 0.519544e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.074 GB / 12.88 M faces
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553393e9 + 0.511313e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.065 GB / 12.88 M faces
 
 
 # Compulsory HBM traffic of one zone-update in every form: the FP64 state
@@ -230,6 +230,42 @@ def oracle_sample(seconds: float, n: int = 64, min_steps: int = 2, nthreads: int
         steps += 1
     el = time.perf_counter() - t0
     return n ** 3 * steps / el, steps, threads
+
+
+def oracle_rate(problems, steps: int, nthreads: int):
+    """Times the oracle (as it stands) advancing every problem by `steps` steps
+    (ghost fill, dt and update, box after box); returns (zone-updates/s, s)."""
+    import oracle
+    work = [(oracle.box_of(pr), oracle.embed(pr.U)) for pr in problems]
+    zones = sum(int(pr.U[0].size) for pr in problems)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for box, Ug in work:
+            oracle.fill_ghosts(box, Ug)
+            dt = oracle.compute_dt(box, Ug)
+            rc, _ = oracle.step(box, Ug, dt, nthreads=nthreads)
+            if rc:
+                raise RuntimeError(f"oracle step failed: {rc}")
+    el = time.perf_counter() - t0
+    return zones * steps / el, el
+
+
+def oracle_configs(threads: int) -> dict:
+    """The oracle on the other workloads, on all cores and on one thread: the
+    Sod 32^3 box in full (20 steps), the first 32 boxes of the 512-box Sedov
+    batch and a 128^3 box of the shear-layer recipe (2 steps each)."""
+    from paper_2007_05218_gb300 import inputs
+    cases = {"sod_32": ("Sod 32^3, the full 20 steps", lambda: [inputs.sod(32, axis=0, nsteps=20)], 20),
+             "sedov_batch_512": ("the first 32 of the 512 Sedov boxes, 2 steps",
+                                 lambda: inputs.sedov_batch(512, seed=0, nsteps=30)[:32], 2),
+             "kelvin_helmholtz_512": ("a 128^3 box of the same shear-layer recipe, 2 steps",
+                                      lambda: [inputs.kelvin_helmholtz(128, seed=0)], 2)}
+    out = {}
+    for name, (sample, make, steps) in cases.items():
+        v, _ = oracle_rate(make(), steps, threads)
+        v1, _ = oracle_rate(make(), steps, 1)
+        out[name] = {"value": v, "cores": threads, "one_thread": v1, "unit": UNIT, "sample": sample}
+    return out
 
 
 def run_reference(args, rank: int) -> None:
@@ -708,7 +744,8 @@ def main() -> None:
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"density wave 64^3 (same recipe), {steps} oracle steps on {threads} threads",
                "one_thread": {"value": v1, "unit": UNIT, "cores": 1,
-                              "sample": f"density wave 32^3 (same recipe), {steps1} oracle steps on 1 thread"}}
+                              "sample": f"density wave 32^3 (same recipe), {steps1} oracle steps on 1 thread"},
+               "configs": oracle_configs(threads)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

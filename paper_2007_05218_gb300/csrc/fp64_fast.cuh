@@ -144,6 +144,12 @@ template <>
 __device__ __forceinline__ double dmin<double>(double a, double b) { return dgt(a, b) ? b : a; }
 template <>
 __device__ __forceinline__ double dmax<double>(double a, double b) { return dgt(b, a) ? b : a; }
+// x > 0 and not NaN (+inf included), on the bit pattern: 0 < bits <= that of +inf
+__device__ __forceinline__ bool pos_not_nan(double x) {
+  const int h = __double2hiint(x);
+  const unsigned l = (unsigned)__double2loint(x);
+  return ((h > 0) | ((h == 0) & (l != 0u))) & ((h < 0x7ff00000) | ((h == 0x7ff00000) & (l == 0u)));
+}
 // x / 2 without an FP64 instruction.  For 2^-1021 <= |x| < inf it is an
 // exponent decrement of the high word.  Below that range the magnitude bits
 // (exponent field 0 or 1) read as an integer M give |x| = M 2^-1074, so x / 2
@@ -174,6 +180,26 @@ __device__ __forceinline__ bool abs_gt_twice<double>(double x, double y) {
   const unsigned h2 = nrm ? hy + (1u << 20) : (hy << 1) | (ly >> 31);
   const unsigned l2 = nrm ? ly : ly << 1;
   return (hy < 0x7fe00000u) & ((hx > h2) | ((hx == h2) & (lx > l2)));
+}
+
+// FP64 -> FP32 rounded to nearest even, on the integer pipe (the conversion
+// instruction occupies the FP64 pipe), as a bit pattern.  Exact for results
+// in the normal FP32 range (|x| in [2^-126, 2^128), where a carry out of the
+// mantissa raises the exponent and rounds the largest values to infinity)
+// and for |x| < 2^-150 (zero, of x's sign).  Everything else (results that
+// are FP32 subnormals, |x| >= 2^128, infinities, NaN) sets `rare`, and the
+// caller converts those with the instruction.
+__device__ __forceinline__ unsigned narrow_bits(double x, bool& rare) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned mh = hi & 0x7fffffffu, sign = hi & 0x80000000u;
+  // exponent field e = mh >> 20: a normal FP32 result for 897 <= e <= 1150
+  const bool normal = mh - (897u << 20) < ((1151u - 897u) << 20);
+  const bool tiny = mh < (873u << 20);  // |x| < 2^-150
+  const unsigned m = ((mh - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u));
+  rare = !normal & !tiny;
+  return tiny ? sign : sign | (m + up);
 }
 
 // FP32 keeps its comparisons and min/max native: the FP32 units are not the

@@ -449,6 +449,7 @@ int hydro_alloc(const hydro_box_desc* d, int nboxes, void* state_dev, size_t sta
     }
     db.gamma = hb.d.gamma;
     db.igm1 = 1.0 / (hb.d.gamma - 1.0);
+    db.gm1 = hb.d.gamma - 1.0;
     db.gamma_f = (float)db.gamma;
     db.igm1_f = (float)db.igm1;
     db.cfl = hb.d.cfl;

@@ -61,6 +61,7 @@ struct DevBox {
   double idx[3];          // 1/dx
   double gamma;
   double igm1;            // 1/(gamma-1)
+  double gm1;             // gamma-1
   double cfl;
   int bc[6];
   float gamma_f, igm1_f;  // FP32 copies for the mixed-precision kernels
@@ -77,6 +78,11 @@ struct BoxRt {
   unsigned int steps;       // updates applied
   float dtdx_f[3];          // FP32 dt/dx per axis for the mixed-precision kernels
   float pad;
+  // FP64 dt/dx per axis and the transverse-correction factors dt/(3 dx) and
+  // dt/(2 dx), each formed once per step by the time-step kernel (as the
+  // products (dt * (1/dx)) * (1/3) and 0.5 * (dt * (1/dx))) instead of in
+  // every thread of the FP64 stages
+  double dtdx[3], dtdx3[3], dtdx2[3];
 };
 
 constexpr unsigned STATUS_NONPHYSICAL = 1u;

@@ -87,7 +87,11 @@ struct Consts<double> {
   static constexpr bool PRIM_RECIPROCALS = true;
   static __device__ __forceinline__ double gamma(const DevBox& b) { return b.gamma; }
   static __device__ __forceinline__ double igm1(const DevBox& b) { return b.igm1; }
-  static __device__ __forceinline__ double dtdx(const DevBox& b, const BoxRt& r, int d) { return r.dt * b.idx[d]; }
+  static __device__ __forceinline__ double gm1(const DevBox& b) { return b.gm1; }
+  // dt/dx, dt/(3 dx) and dt/(2 dx), formed once per step by the time-step kernel
+  static __device__ __forceinline__ double dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx[d]; }
+  static __device__ __forceinline__ double dtdx3(const DevBox&, const BoxRt& r, int d) { return r.dtdx3[d]; }
+  static __device__ __forceinline__ double dtdx2(const DevBox&, const BoxRt& r, int d) { return r.dtdx2[d]; }
 };
 template <>
 struct Consts<float> {
@@ -97,7 +101,12 @@ struct Consts<float> {
   static constexpr bool PRIM_RECIPROCALS = false;
   static __device__ __forceinline__ float gamma(const DevBox& b) { return b.gamma_f; }
   static __device__ __forceinline__ float igm1(const DevBox& b) { return b.igm1_f; }
+  static __device__ __forceinline__ float gm1(const DevBox& b) { return b.gamma_f - 1.0f; }
   static __device__ __forceinline__ float dtdx(const DevBox&, const BoxRt& r, int d) { return r.dtdx_f[d]; }
+  static __device__ __forceinline__ float dtdx3(const DevBox&, const BoxRt& r, int d) {
+    return r.dtdx_f[d] * float(1.0 / 3.0);
+  }
+  static __device__ __forceinline__ float dtdx2(const DevBox&, const BoxRt& r, int d) { return 0.5f * r.dtdx_f[d]; }
 };
 
 template <typename R>
@@ -281,11 +290,11 @@ __device__ __forceinline__ void body_prim(const TableView& tv, const int blk_, c
       w = __ddiv_rn(U[3 * vs + Z], rho);
       const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
       const double kin = __dmul_rn(__dmul_rn(0.5, rho), uu);
-      p = __dmul_rn(__dsub_rn(b.gamma, 1.0), __dsub_rn(U[4 * vs + Z], kin));
+      p = __dmul_rn(b.gm1, __dsub_rn(U[4 * vs + Z], kin));
       if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
       cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(b.gamma, p), rho));
     } else {
-      const PrimZone pz = prim_zone(rho, U[vs + Z], U[2 * vs + Z], U[3 * vs + Z], U[4 * vs + Z], b.gamma);
+      const PrimZone pz = prim_zone(rho, U[vs + Z], U[2 * vs + Z], U[3 * vs + Z], U[4 * vs + Z], b.gamma, b.gm1);
       rho = pz.rho;
       u = pz.u;
       v = pz.v;
@@ -309,7 +318,7 @@ __device__ __forceinline__ void body_prim(const TableView& tv, const int blk_, c
       }
       W[FLD_IC * vs + Z] = ic;
       W[FLD_CR * vs + Z] = cs * ir;
-    } else {
+    } else if constexpr (EXACT) {  // conversion instructions (this form is bound by its IEEE divides)
       float* W = fields<float>(work, b);
       W[Z] = (float)rho;
       W[vs + Z] = (float)u;
@@ -317,6 +326,27 @@ __device__ __forceinline__ void body_prim(const TableView& tv, const int blk_, c
       W[3 * vs + Z] = (float)w;
       W[4 * vs + Z] = (float)p;
       W[FLD_C * vs + Z] = (float)cs;
+    } else {
+      // rounded to FP32 on the integer pipe (bitwise the conversion); a warp
+      // converts with the instruction only where a lane holds a value outside
+      // the normal FP32 range (other than a zero-bound one)
+      float* W = fields<float>(work, b);
+      const double q[6] = {rho, u, v, w, p, cs};
+      unsigned r[6], defer = 0u;
+#pragma unroll
+      for (int m = 0; m < 6; m++) {
+        bool x;
+        r[m] = narrow_bits(q[m], x);
+        defer |= (unsigned)x << m;
+      }
+      if (__any_sync(__activemask(), defer != 0u)) {
+#pragma unroll
+        for (int m = 0; m < 6; m++)
+          if ((defer >> m) & 1u) r[m] = __float_as_uint(__double2float_rn(q[m]));
+      }
+      const int slot[6] = {0, 1, 2, 3, 4, FLD_C};
+#pragma unroll
+      for (int m = 0; m < 6; m++) W[slot[m] * vs + Z] = __uint_as_float(r[m]);
     }
     if (c[0] >= 0 && c[0] < b.n[0] && c[1] >= 0 && c[1] < b.n[1] && c[2] >= 0 && c[2] < b.n[2]) {
       const double s = signal_rate(u, v, w, cs, b.idx);
@@ -348,6 +378,18 @@ __global__ void __launch_bounds__(256) k_prim(TableView tv, const DevBox* __rest
   body_prim<EXACT>(tv, blockIdx.x, boxes, state, work, rt);
 }
 
+// dt/dx per axis in both compute types and the FP64 transverse-correction
+// factors of the step, formed once per box
+__device__ __forceinline__ void set_factors(BoxRt& r, double dt, const double* idx) {
+  for (int a = 0; a < 3; a++) {
+    const double f = __dmul_rn(dt, idx[a]);
+    r.dtdx[a] = f;
+    r.dtdx3[a] = __dmul_rn(f, 1.0 / 3.0);
+    r.dtdx2[a] = __dmul_rn(0.5, f);
+    r.dtdx_f[a] = (float)f;
+  }
+}
+
 // The time step of box b: dt_in[b] if given, else cfl / (largest signal rate,
 // reduced by the primitive stage); the reduction slot is cleared for the
 // next step.
@@ -357,7 +399,7 @@ __device__ __noinline__ void b_dt_box(const DevBox* boxes, BoxRt* rt, int b, con
   const double dt = dt_in ? dt_in[b] : boxes[b].cfl / smax;
   rt[b].smax = 0ull;
   rt[b].dt = dt;
-  for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
+  set_factors(rt[b], dt, boxes[b].idx);
   if (dt_out) dt_out[b] = dt;
   if (advance) {
     rt[b].time += dt;
@@ -394,7 +436,7 @@ __global__ void __launch_bounds__(256) k_dt_shared(const DevBox* __restrict__ bo
     if (boxes[b].n[0] == 0) continue;
     rt[b].smax = 0ull;
     rt[b].dt = dt;
-    for (int a = 0; a < 3; a++) rt[b].dtdx_f[a] = (float)(dt * boxes[b].idx[a]);
+    set_factors(rt[b], dt, boxes[b].idx);
     if (dt_out) dt_out[b] = dt;
     if (advance) {
       rt[b].time += dt;
@@ -979,8 +1021,7 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // reciprocals; wave-speed min/max and sign tests run on the integer pipe in
 // FP64.
 template <typename R>
-__device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R* F) {
-  const R gm1 = gamma - R(1);
+__device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R* F) {
   const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
   const R rr = Rs[0], ur = Rs[1], vr = Rs[2], wr = Rs[3], pr = Rs[4];
   // 1/sqrt(rho) of each side: from the caller where SHARE_RSQRT holds
@@ -1130,9 +1171,10 @@ __device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R ig
 // rsr their 1/sqrt(rho) (HLLC uses them; the two-shock flux is built from the
 // sampled state alone).
 template <typename R, int RS>
-__device__ __forceinline__ void riemann(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R igm1, R* F) {
+__device__ __forceinline__ void riemann(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R igm1,
+                                        R* F) {
   if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock(L, Rs, gamma, igm1, F);
-  else hllc(L, El, rsl, Rs, Er, rsr, gamma, F);
+  else hllc(L, El, rsl, Rs, Er, rsr, gamma, gm1, F);
 }
 
 // The two states of the D-face at zone Z: primitive q (5) and conserved
@@ -1179,7 +1221,7 @@ __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W,
   const bool own = RS == HYDRO_RIEMANN_HLLC && Consts<R>::SHARE_RSQRT;
   const R rsl = own ? nr_rsqrt(qL[0]) : R(0);
   const R rsr = own ? nr_rsqrt(qR[0]) : R(0);
-  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, Consts<R>::gamma(b), Consts<R>::gm1(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
@@ -1235,7 +1277,7 @@ __device__ __forceinline__ void flux_deltas(const R* const* Fb, const long long*
 
 // The correction itself, from the flux differences (see correct).
 template <typename R, int NT>
-__device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], const R* fac, R gamma, R igm1,
+__device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], const R* fac, R gm1, R igm1,
                                         R& rs) {
   R U[5] = {q[0], u[0], u[1], u[2], u[3]};
 #pragma unroll
@@ -1248,7 +1290,7 @@ __device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], con
     const R ir = Consts<R>::SHARE_RSQRT ? r * r : nr_rcp(U[0]);
     const R uu = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
     const R kin = half_of(U[1] * uu + U[2] * v + U[3] * w);
-    const R p = (gamma - R(1)) * (U[4] - kin);
+    const R p = gm1 * (U[4] - kin);
     if (is_pos(p)) {
       q[0] = U[0];
       q[1] = uu;
@@ -1269,10 +1311,10 @@ __device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], con
 
 template <typename R, int D, int NT>
 __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
-                                     long long vs, long long Z, R gamma, R igm1, R& rs) {
+                                     long long vs, long long Z, R gm1, R igm1, R& rs) {
   R dlt[NT][5];
   flux_deltas<R, D, NT>(Fb, st, vs, Z, dlt);
-  return correct_by<R, NT>(q, u, dlt, fac, gamma, igm1, rs);
+  return correct_by<R, NT>(q, u, dlt, fac, gm1, igm1, rs);
 }
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
@@ -1285,7 +1327,7 @@ template <typename R, int D, int T, int RS>
 __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
                                           const R* qL0, const R* uL, const R* qR0, const R* uR) {
   const long long vs = b.vs, sD = b.s[D];
-  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  const R gamma = Consts<R>::gamma(b), gm1 = Consts<R>::gm1(b), igm1 = Consts<R>::igm1(b);
   R qL[5], qR[5], Fn[5];
 #pragma unroll
   for (int m = 0; m < 5; m++) {
@@ -1294,11 +1336,11 @@ __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, lo
   }
   const R* Fb[1] = {W + (FLD_F0 + 5 * T) * vs};
   const long long st[1] = {b.s[T]};
-  const R fac[1] = {Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0)};
+  const R fac[1] = {Consts<R>::dtdx3(b, rt, T)};
   R rsl, rsr;
-  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1, rsl);
-  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1, rsr);
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, igm1, Fn);
+  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
+  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * vs, vs, Z, Fn);
 }
 
@@ -1368,16 +1410,16 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
                                           bool wall) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
   const long long vs = b.vs, sD = b.s[D];
-  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  const R gamma = Consts<R>::gamma(b), gm1 = Consts<R>::gm1(b), igm1 = Consts<R>::igm1(b);
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, vs, Z, sD, igm1, qL, uL, qR, uR);
   const R* Fb[2] = {W + (FLD_F1 + 5 * pair_slot(E, F)) * vs, W + (FLD_F1 + 5 * pair_slot(F, E)) * vs};
   const long long st[2] = {b.s[E], b.s[F]};
-  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
+  const R fac[2] = {Consts<R>::dtdx2(b, rt, E), Consts<R>::dtdx2(b, rt, F)};
   R rsl, rsr;
-  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gamma, igm1, rsl);
-  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gamma, igm1, rsr);
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, igm1, Fn);
+  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
+  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
   if (wall) {
     // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
     Fn[0] = R(0);
@@ -1448,14 +1490,14 @@ __device__ __forceinline__ void line_store_edges(R* __restrict__ W, long long vs
 template <typename R, int D, int RS>
 __device__ __forceinline__ void line_normal_flux(const DevBox& b, R* __restrict__ W, long long Z, const R* qL,
                                                  const R* qR) {
-  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  const R gamma = Consts<R>::gamma(b), gm1 = Consts<R>::gm1(b), igm1 = Consts<R>::igm1(b);
   R uL[4], uR[4], Fn[5];
   conserved_of(qL, igm1, uL);
   conserved_of(qR, igm1, uR);
   const bool own = RS == HYDRO_RIEMANN_HLLC && Consts<R>::SHARE_RSQRT;
   const R rsl = own ? nr_rsqrt(qL[0]) : R(0);
   const R rsr = own ? nr_rsqrt(qR[0]) : R(0);
-  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, gamma, igm1, Fn);
+  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, gamma, gm1, igm1, Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
@@ -1650,12 +1692,12 @@ template <typename R, int D>
 __device__ __forceinline__ void ctu2_correct(const DevBox& b, Ctu2Zone<R, D>& z, const R* fac, R& Em, R& rsm,
                                              R& Ep, R& rsp) {
   static_assert(!Consts<R>::STORE_CONSERVED, "zone-wise stage 2 runs for FP32 boxes");
-  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  const R gamma = Consts<R>::gamma(b), gm1 = Consts<R>::gm1(b), igm1 = Consts<R>::igm1(b);
   R um[4], up[4];
   conserved_of(z.qm, igm1, um);
   conserved_of(z.qp, igm1, up);
-  Em = correct_by<R, 2>(z.qm, um, z.dlt, fac, gamma, igm1, rsm);
-  Ep = correct_by<R, 2>(z.qp, up, z.dlt, fac, gamma, igm1, rsp);
+  Em = correct_by<R, 2>(z.qm, um, z.dlt, fac, gm1, igm1, rsm);
+  Ep = correct_by<R, 2>(z.qp, up, z.dlt, fac, gm1, igm1, rsp);
 }
 
 // Final flux through the low D-face of zone Z from the corrected states.
@@ -1663,7 +1705,7 @@ template <typename R, int D, int RS>
 __device__ __forceinline__ void ctu2_flux(const DevBox& b, R* __restrict__ W, long long Z, int face, R* qL, R EL,
                                           R rsl, R* qR, R ER, R rsr) {
   R Fn[5];
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::gm1(b), Consts<R>::igm1(b), Fn);
   const bool wall = (face == 0 && b.bc[2 * D] == HYDRO_BC_REFLECT && b.nbr1[2 * D] == 0) ||
                     (face == b.n[D] && b.bc[2 * D + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * D + 1] == 0);
   if (wall) {  // impermeable: only the normal momentum flux (the wall pressure) remains
@@ -1689,7 +1731,7 @@ __device__ __forceinline__ void ctu2_x(const DevBox& b, R* __restrict__ W, long 
   const int lane = rem & 31;
   const int i = -1 + 31 * (rem >> 5) + lane;
   const long long Z = zone(b, min(i, nx), (int)(row % ny), (int)(row / ny));
-  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, 1), R(0.5) * Consts<R>::dtdx(b, rt, 2)};
+  const R fac[2] = {Consts<R>::dtdx2(b, rt, 1), Consts<R>::dtdx2(b, rt, 2)};
   Ctu2Zone<R, 0> z;
   R Em, Ep, rsm, rsp;
   ctu2_load<R, 0>(b, W, Z, z);
@@ -1719,7 +1761,7 @@ __device__ __forceinline__ void ctu2_walk(const DevBox& b, R* __restrict__ W, lo
   c[D] = fs - 1;
   const long long sD = b.s[D];
   long long Z = zone(b, c[0], c[1], c[2]);
-  const R fac[2] = {R(0.5) * Consts<R>::dtdx(b, rt, E), R(0.5) * Consts<R>::dtdx(b, rt, F)};
+  const R fac[2] = {Consts<R>::dtdx2(b, rt, E), Consts<R>::dtdx2(b, rt, F)};
   Ctu2Zone<R, D> z;
   R ql[5] = {}, El = R(0), rsl = R(0);
   ctu2_load<R, D>(b, W, Z, z);
@@ -1794,20 +1836,20 @@ template <typename R, int D, int T>
 __device__ __forceinline__ void ctu1_correct(const DevBox& b, Ctu1Zone<R, D, T>& z, R fac, R& Em, R& rsm, R& Ep,
                                              R& rsp) {
   static_assert(!Consts<R>::STORE_CONSERVED, "zone-wise stage 1 runs for FP32 boxes");
-  const R gamma = Consts<R>::gamma(b), igm1 = Consts<R>::igm1(b);
+  const R gamma = Consts<R>::gamma(b), gm1 = Consts<R>::gm1(b), igm1 = Consts<R>::igm1(b);
   R um[4], up[4];
   conserved_of(z.qm, igm1, um);
   conserved_of(z.qp, igm1, up);
   const R f1[1] = {fac};
-  Em = correct_by<R, 1>(z.qm, um, z.dlt, f1, gamma, igm1, rsm);
-  Ep = correct_by<R, 1>(z.qp, up, z.dlt, f1, gamma, igm1, rsp);
+  Em = correct_by<R, 1>(z.qm, um, z.dlt, f1, gm1, igm1, rsm);
+  Ep = correct_by<R, 1>(z.qp, up, z.dlt, f1, gm1, igm1, rsp);
 }
 
 template <typename R, int D, int T, int RS>
 __device__ __forceinline__ void ctu1_store(const DevBox& b, R* __restrict__ W, long long Z, R* qL, R EL, R rsl,
                                            R* qR, R ER, R rsr) {
   R Fn[5];
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::igm1(b), Fn);
+  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, Consts<R>::gamma(b), Consts<R>::gm1(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * b.vs, b.vs, Z, Fn);
 }
 
@@ -1835,7 +1877,7 @@ __device__ __forceinline__ void ctu1_x(const DevBox& b, R* __restrict__ W, long 
   Ctu1Zone<R, 0, T> z;
   R ql[5], Em, Ep, rsm, rsp;
   ctu1_load<R, 0, T>(b, W, Z, z);
-  ctu1_correct<R, 0, T>(b, z, Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0), Em, rsm, Ep, rsp);
+  ctu1_correct<R, 0, T>(b, z, Consts<R>::dtdx3(b, rt, T), Em, rsm, Ep, rsp);
 #pragma unroll
   for (int m = 0; m < 5; m++) ql[m] = __shfl_up_sync(0xffffffffu, z.qp[m], 1);
   const R El = __shfl_up_sync(0xffffffffu, Ep, 1), rsl = __shfl_up_sync(0xffffffffu, rsp, 1);
@@ -1868,7 +1910,7 @@ __device__ __forceinline__ void ctu1_walk(const DevBox& b, R* __restrict__ W, lo
   c[D] = fs - 1;
   const long long sD = b.s[D];
   long long Z = zone(b, c[0], c[1], c[2]);
-  const R fac = Consts<R>::dtdx(b, rt, T) * R(1.0 / 3.0);
+  const R fac = Consts<R>::dtdx3(b, rt, T);
   Ctu1Zone<R, D, T> z;
   R ql[5] = {}, El = R(0), rsl = R(0);
   ctu1_load<R, D, T>(b, W, Z, z);
@@ -1930,9 +1972,8 @@ __device__ __forceinline__ double widen(double x) { return x; }
 // FP64 for every box; the fluxes are read in the box's compute type.
 template <typename R>
 __device__ __forceinline__ void update_zone(const DevBox& b, double* __restrict__ U, const R* __restrict__ W,
-                                            long long Z, double dt, double* nu) {
+                                            long long Z, const double* dtdx, double* nu) {
   const long long vs = b.vs;
-  const double dtdx[3] = {dt * b.idx[0], dt * b.idx[1], dt * b.idx[2]};
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     double val = U[v * vs + Z];
@@ -1954,18 +1995,18 @@ __device__ __forceinline__ void body_update(const TableView& tv, const int blk_,
   if (!decode(t_, lo, ext, c)) return;
   const long long Z = zone(b, c[0], c[1], c[2]);
   double* U = state + b.state_off;
-  const double dt = rt[bi].dt;
+  const double dtdx[3] = {rt[bi].dtdx[0], rt[bi].dtdx[1], rt[bi].dtdx[2]};
   double nu[5];
-  if (b.precision == HYDRO_FP64) update_zone(b, U, fields<double>(work, b), Z, dt, nu);
-  else update_zone(b, U, fields<float>(work, b), Z, dt, nu);
-  // rho > 0 and p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0, i.e. 2 rho E > |m|^2:
-  // no reciprocal; a NaN fails the tests
+  if (b.precision == HYDRO_FP64) update_zone(b, U, fields<double>(work, b), Z, dtdx, nu);
+  else update_zone(b, U, fields<float>(work, b), Z, dtdx, nu);
+  // rho > 0 and p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0, i.e. rho E > |m|^2 / 2:
+  // no reciprocal; a NaN fails the tests.  One fused multiply-add forms
+  // rho E - |m|^2 / 2, half of 2 rho E - |m|^2 and so of its sign (the
+  // halving is exact for |m|^2 >= 2^-1021; the two differ only where the
+  // difference underflows).
   const double m2 = nu[1] * nu[1] + nu[2] * nu[2] + nu[3] * nu[3];
-  // is_pos reads bit patterns, under which a NaN with a clear sign bit counts
-  // as positive; e2 != e2 catches every NaN (one in the density, the energy or
-  // a momentum makes e2 NaN)
-  const double e2 = 2.0 * nu[0] * nu[4] - m2;
-  if (!is_pos(nu[0]) || !is_pos(e2) || e2 != e2) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
+  const double e2 = fma(nu[0], nu[4], -half_of(m2));
+  if (!is_pos(nu[0]) || !pos_not_nan(e2)) atomicOr(&rt[bi].status, STATUS_NONPHYSICAL);
 }
 
 // out-of-line copy for the persistent kernel
@@ -2034,10 +2075,11 @@ __device__ __forceinline__ EdgeF tile_correct1(const float* q, const float (*dlt
                                                float igm1) {
   EdgeF e;
   float u[4];
+  const float gm1 = gamma - 1.0f;
 #pragma unroll
   for (int m = 0; m < 5; m++) e.q[m] = q[m];
   conserved_of(e.q, igm1, u);
-  e.E = correct_by<float, NT>(e.q, u, dlt, fac, gamma, igm1, e.rs);
+  e.E = correct_by<float, NT>(e.q, u, dlt, fac, gm1, igm1, e.rs);
   return e;
 }
 
@@ -2052,7 +2094,8 @@ __device__ __forceinline__ void tile_correct(const float* qm, const float* qp, c
 // Riemann flux between two corrected states, in the normal frame of D.
 template <int RS>
 __device__ __forceinline__ void tile_flux(const EdgeF& l, const EdgeF& r, float gamma, float igm1, float* Fn) {
-  riemann<float, RS>(l.q, l.E, l.rs, r.q, r.E, r.rs, gamma, igm1, Fn);
+  const float gm1 = gamma - 1.0f;
+  riemann<float, RS>(l.q, l.E, l.rs, r.q, r.E, r.rs, gamma, gm1, igm1, Fn);
 }
 
 // Flux difference across a zone for the normal frame of D: F[comp<D>(m)] at
@@ -2147,7 +2190,7 @@ __global__ void __launch_bounds__(TileShape<TY>::NR, 1)
   float* W = fields<float>(work, b);
   double* U = state + b.state_off;
   const BoxRt& r = rt[bi];
-  const float gamma = b.gamma_f, igm1 = b.igm1_f;
+  const float gamma = b.gamma_f, gm1 = gamma - 1.0f, igm1 = b.igm1_f;
   const float dtdx[3] = {r.dtdx_f[0], r.dtdx_f[1], r.dtdx_f[2]};
   const double dtdx64[3] = {r.dt * b.idx[0], r.dt * b.idx[1], r.dt * b.idx[2]};
   const float fac1[3] = {dtdx[0] * float(1.0 / 3.0), dtdx[1] * float(1.0 / 3.0), dtdx[2] * float(1.0 / 3.0)};
@@ -2298,7 +2341,7 @@ __global__ void __launch_bounds__(TileShape<TY>::NR, 1)
         }
         conserved_of(qL, igm1, uL);
         conserved_of(qR, igm1, uR);
-        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, gm1, igm1, Fn);
         tile_store<0>(f0x_c, NR, t, Fn);
       }
       if (fc_y && in_x) {
@@ -2309,7 +2352,7 @@ __global__ void __launch_bounds__(TileShape<TY>::NR, 1)
         }
         conserved_of(qL, igm1, uL);
         conserved_of(qR, igm1, uR);
-        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, gm1, igm1, Fn);
         tile_store<1>(f0y_c, NR, t, Fn);
       }
       if (p >= z0 && in_x && in_y) {
@@ -2320,7 +2363,7 @@ __global__ void __launch_bounds__(TileShape<TY>::NR, 1)
         }
         conserved_of(qL, igm1, uL);
         conserved_of(qR, igm1, uR);
-        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, igm1, Fn);
+        riemann<float, RS>(qL, uL[3], 0.0f, qR, uR[3], 0.0f, gamma, gm1, igm1, Fn);
         tile_store<2>(f0z_c, NR, t, Fn);
       }
     }

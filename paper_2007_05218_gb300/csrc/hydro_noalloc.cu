@@ -33,6 +33,7 @@ struct DtBox {
   long long pitch, plane, vs, state_off;
   double idx[3];
   double gamma;
+  double gm1;  // gamma - 1
   double cfl;
 };
 
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_speed(DtScratch* __restrict__
     const int j = (int)(r - (long long)k * b.n[1]);
     const long long Z = b.state_off + (i + HYDRO_NG) + (j + HYDRO_NG) * b.pitch + (k + HYDRO_NG) * b.plane;
     const hydro::PrimZone z = hydro::prim_zone(state[Z], state[Z + b.vs], state[Z + 2 * b.vs],
-                                               state[Z + 3 * b.vs], state[Z + 4 * b.vs], b.gamma);
+                                               state[Z + 3 * b.vs], state[Z + 4 * b.vs], b.gamma, b.gm1);
     const unsigned long long s = (unsigned long long)__double_as_longlong(hydro::signal_rate(z.u, z.v, z.w, z.cs, b.idx));
     sbits = s > sbits ? s : sbits;  // non-negative doubles order like their bit patterns
   }
@@ -166,6 +167,7 @@ extern "C" int hydro_compute_dt_noalloc(const hydro_box_desc* d, int nboxes, con
     b.idx[1] = 1.0 / d[i].dy;
     b.idx[2] = 1.0 / d[i].dz;
     b.gamma = d[i].gamma;
+    b.gm1 = d[i].gamma - 1.0;
     b.cfl = d[i].cfl;
     const long long n = (long long)d[i].nx * d[i].ny * d[i].nz;
     start[i] = (int)blocks;

@@ -187,6 +187,7 @@ hydro::DevBox dev_box(const Request* r) {
   }
   db.gamma = hb.d.gamma;
   db.igm1 = 1.0 / (hb.d.gamma - 1.0);
+  db.gm1 = hb.d.gamma - 1.0;
   db.gamma_f = (float)db.gamma;
   db.igm1_f = (float)db.igm1;
   db.cfl = hb.d.cfl;

@@ -5,6 +5,7 @@
 // rho is floored at SMALL_DENS, u = m / rho from one refined reciprocal,
 // p = (gamma - 1)(E - rho/2 |u|^2) floored at SMALL_PRES, and one refined
 // reciprocal square root of c^2 = gamma p / rho gives 1/c and c = c^2 (1/c).
+// gm1 = gamma - 1 (the box's stored difference, the same double).
 #pragma once
 
 #include "fp64_fast.cuh"
@@ -19,7 +20,7 @@ struct PrimZone {
 };
 
 __device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, double mz, double E,
-                                              double gamma) {
+                                              double gamma, double gm1) {
   // every operation written out with its rounding (fused where the product
   // feeds a sum), so that no kernel that inlines this can contract it
   // differently from another
@@ -31,7 +32,7 @@ __device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, 
   z.v = __dmul_rn(my, z.ir);
   z.w = __dmul_rn(mz, z.ir);
   const double uu = __fma_rn(z.w, z.w, __fma_rn(z.v, z.v, __dmul_rn(z.u, z.u)));
-  double p = __dmul_rn(__dsub_rn(gamma, 1.0), __fma_rn(__dmul_rn(-0.5, rho), uu, E));
+  double p = __dmul_rn(gm1, __fma_rn(__dmul_rn(-0.5, rho), uu, E));
   if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
   z.p = p;
   const double c2 = __dmul_rn(__dmul_rn(gamma, p), z.ir);
@@ -40,8 +41,18 @@ __device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, 
   return z;
 }
 
-// max over the axes d of (|u_d| + c) / dx_d, given idx[d] = 1 / dx_d
+// max over the axes d of (|u_d| + c) / dx_d, given idx[d] = 1 / dx_d.  With
+// one 1/dx for all axes (cubic zones) it is (max_d |u_d| + c) / dx: rounded
+// addition and multiplication by a positive number are non-decreasing, so
+// taking the maximum first gives the same double, for one addition and one
+// multiplication instead of three each (the test and the maximum of the
+// magnitudes run on the integer pipe).
+__device__ __forceinline__ bool same_double(double a, double b) {
+  return ((__double2hiint(a) ^ __double2hiint(b)) | (__double2loint(a) ^ __double2loint(b))) == 0;
+}
 __device__ __forceinline__ double signal_rate(double u, double v, double w, double cs, const double* idx) {
+  if (same_double(idx[0], idx[1]) & same_double(idx[1], idx[2]))
+    return __dmul_rn(__dadd_rn(dmax(dmax(fabs(u), fabs(v)), fabs(w)), cs), idx[0]);
   return dmax(dmax(__dmul_rn(__dadd_rn(fabs(u), cs), idx[0]), __dmul_rn(__dadd_rn(fabs(v), cs), idx[1])),
               __dmul_rn(__dadd_rn(fabs(w), cs), idx[2]));
 }

@@ -1,6 +1,8 @@
 // Checks the device arithmetic helpers of fp64_fast.cuh on the GPU against
 // IEEE operations: the bit-pattern sign tests, comparisons, min/max, exact
-// halving and the |x| > 2|y| test bit for bit, on patterns drawn over every
+// halving, the |x| > 2|y| test and the integer FP64 -> FP32 rounding (against
+// the conversion instruction, where it does not defer to it) bit for bit, on
+// patterns drawn over every
 // exponent (subnormals, the range edges, zero and both signs included); the
 // Newton-refined reciprocal, reciprocal square root and square root within
 // their stated error over normal arguments.  Prints one line per check and
@@ -18,7 +20,7 @@
 
 using namespace hydro;
 
-enum { BAD_HALF, BAD_CMP, BAD_RCP, BAD_SQRT, BAD_RSQRT, NBAD };
+enum { BAD_HALF, BAD_CMP, BAD_RCP, BAD_SQRT, BAD_RSQRT, BAD_NARROW, NBAD };
 
 __device__ double ulp_of(double r) { return ldexp(1.0, ilogb(r) - 52); }
 
@@ -28,6 +30,13 @@ __global__ void check_bits(const double* x, const double* y, int n, unsigned lon
   const double a = x[i], c = y[i];
   const double h = half_of<double>(a), r = __dmul_rn(0.5, a);
   if (!(__double_as_longlong(h) == __double_as_longlong(r) || (isnan(h) && isnan(r)))) atomicAdd(&bad[BAD_HALF], 1ull);
+  bool rare;
+  const unsigned nb = narrow_bits(a, rare);
+  if (!rare && nb != __float_as_uint(__double2float_rn(a))) atomicAdd(&bad[BAD_NARROW], 1ull);
+  // what it defers: FP32 subnormal results, |x| >= 2^128, infinities and NaN, and nothing else
+  const double m = fabs(a);
+  const bool expect_rare = isnan(a) || m >= 0x1p128 || (m >= 0x1p-150 && m < 0x1p-126);
+  if (rare != expect_rare) atomicAdd(&bad[BAD_NARROW], 1ull);
   if (!isfinite(a) || !isfinite(c)) return;
   bool e = abs_gt_twice<double>(a, c) != (fabs(a) > __dmul_rn(2.0, fabs(c)));
   e |= is_pos<double>(a) != (a > 0.0);
@@ -97,6 +106,17 @@ int main() {
     x.push_back(from_pattern(p));
     y.push_back(from_pattern(q));
   }
+  // patterns around the FP32 range for the narrowing: exponents 2^-163 .. 2^137,
+  // with the dropped 29 mantissa bits at and next to the rounding tie
+  for (int i = 0; i < (1 << 21); i++) {
+    const uint64_t e = 860 + g() % 301;
+    uint64_t mant = g() & 0x000fffffffffffffull;
+    if (i % 4 == 1) mant = (mant & ~0x1fffffffull) | 0x10000000ull;                    // a tie
+    if (i % 4 == 2) mant = (mant & ~0x1fffffffull) | (0x10000000ull + (g() % 3) - 1);  // next to it
+    if (i % 8 == 3) mant |= 0x000fffffe0000000ull;                                     // all ones above: carry
+    x.push_back(from_pattern((g() & (1ull << 63)) | (e << 52) | mant));
+    y.push_back(from_pattern(g()));
+  }
   // normal positive arguments for the refined operations, 2^-1000 .. 2^1000
   std::vector<double> z(1 << 22);
   for (double& v : z) v = from_pattern(((uint64_t)(23 + g() % 2001) << 52) | (g() & 0x000fffffffffffffull));
@@ -121,8 +141,8 @@ int main() {
   cudaMemcpy(bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost);
   cudaMemcpy(worst, dworst, sizeof(worst), cudaMemcpyDeviceToHost);
   std::printf("cuda %s\n", cudaGetErrorString(err));
-  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu\n", n, bad[BAD_HALF],
-              bad[BAD_CMP]);
+  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu, narrowing mismatches %llu\n",
+              n, bad[BAD_HALF], bad[BAD_CMP], bad[BAD_NARROW]);
   std::printf("refined cases %d: rcp > 2 ulp %llu (max %.3f), sqrt > 2 ulp %llu (max %.3f), rsqrt > 2^-51.5 %llu "
               "(max %.3f x 2^-53)\n",
               nz, bad[BAD_RCP], worst[0] / 1000.0, bad[BAD_SQRT], worst[1] / 1000.0, bad[BAD_RSQRT],
