@@ -64,7 +64,7 @@ FLOPS_PER_UNIT = {
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
 # stands; a stage missing here has no capture of its current code and reports
 # traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553393e9 + 0.511313e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.065 GB / 12.88 M faces
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553415e9 + 0.508914e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.062 GB / 12.88 M faces
 
 
 # Compulsory HBM traffic of one zone-update in every form: the FP64 state
@@ -725,6 +725,9 @@ def main() -> None:
                 "traffic": (TRAFFIC_BYTES_PER_UNIT[top] * units_per_launch(top, n)
                             if top in TRAFFIC_BYTES_PER_UNIT else None),
                 "peak_source": "derived from unit counts and clocks: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
+                "note": ("the kernel forms its FP64 products (45 of the 129 FP64 operations of a corrected face) "
+                         "on the integer pipe, bitwise the FP64 multiply; achieved counts all of its algorithmic "
+                         "flops against the FP64 pipe's peak, so frac can pass what that pipe alone delivers"),
                 "peak_measured": fp64_probe / 1e12, "frac_of_measured": achieved / fp64_probe,
                 "peak_measured_source": "FP64 multiply-add probe on every SM (hydro_measure_peaks), this run",
                 "kernel_time_source": f"events around each stage launch, {nprof} profiled steps after the timed region",

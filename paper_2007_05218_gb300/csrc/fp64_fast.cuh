@@ -30,6 +30,82 @@
 
 namespace hydro {
 
+// FP64 product on the integer pipe.  GB300's FP64 pipe is the scarce unit of
+// the FP64 kernels while its integer pipe idles, and a correctly rounded
+// product needs only 32-bit integer work: the 106-bit product of the two
+// 53-bit significands from four 32 x 32 -> 64-bit multiply-adds, a one-bit
+// normalisation, round to nearest even on the dropped bits (guard bit, then
+// sticky or the kept lsb), and the exponent added to the significand with its
+// leading bit (so that a carry out of the rounding raises the exponent, and
+// rounding past the largest binade gives infinity).  Bitwise __dmul_rn for
+// normal or zero operands whose product is normal or zero; for any other
+// operands (subnormal, infinite or NaN, or a product that underflows or
+// overflows) it sets `bad`, and the caller recomputes with the FP64
+// instruction.  tests/fp64_helpers_check.cu compares it with __dmul_rn bit
+// for bit over every exponent pair.
+__device__ __forceinline__ double imul_rn(double a, double b, unsigned& bad) {
+  const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
+  const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
+  const unsigned ea = (ah >> 20) & 0x7ffu, eb = (bh >> 20) & 0x7ffu;
+  const unsigned mah = (ah & 0xfffffu) | 0x100000u, mbh = (bh & 0xfffffu) | 0x100000u;
+  // P = ma mb = up 2^64 + w1 2^32 + w0, up < 2^42
+  const unsigned long long ll = (unsigned long long)al * bl;
+  const unsigned long long t1 = (unsigned long long)mah * bl + (ll >> 32);
+  const unsigned long long t2 = (unsigned long long)al * mbh + (unsigned)t1;
+  const unsigned w0 = (unsigned)ll, w1 = (unsigned)t2;
+  const unsigned long long up = (unsigned long long)mah * mbh + ((t1 >> 32) + (t2 >> 32));
+  const unsigned uh = (unsigned)(up >> 32), ul = (unsigned)up;
+  const unsigned top = (uh >> 9) & 1u;  // P >= 2^105
+  const unsigned sh = 12u - top;        // the 53 kept bits end at bit 52 + top of P
+  unsigned ml = __funnelshift_l(w1, ul, sh), mh = __funnelshift_l(ul, uh, sh);
+  const unsigned rem = w1 << sh;  // the dropped bits of w1, guard bit first
+  const unsigned inc = (rem >> 31) & ((((rem & 0x7fffffffu) | w0) != 0u) | (ml & 1u));
+  const unsigned ml2 = ml + inc;
+  mh += ml2 < ml ? 1u : 0u;
+  ml = ml2;
+  const int e = (int)(ea + eb + top) - 1023;  // biased exponent of the product
+  const unsigned sign = (ah ^ bh) & 0x80000000u;
+  const bool za = ((ah & 0x7fffffffu) | al) == 0u, zb = ((bh & 0x7fffffffu) | bl) == 0u;
+  const bool zero = (za & (eb < 2047u)) | (zb & (ea < 2047u));  // zero times a finite number
+  const bool ok = ((ea - 1u < 2046u) & (eb - 1u < 2046u) & ((unsigned)(e - 1) < 2046u)) | zero;
+  bad |= ok ? 0u : 1u;
+  return zero ? __hiloint2double((int)sign, 0)
+              : __hiloint2double((int)((((unsigned)(e - 1) << 20) + mh) | sign), (int)ml);
+}
+
+// The FP64 multiply instruction where the integer product set `bad`: volatile,
+// so that the compiler keeps it inside the rarely taken recomputation instead
+// of issuing it in every warp.
+__device__ __forceinline__ double dmul_insn(double a, double b) {
+  double r;
+  asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+
+// Multiplication policies for the stage arithmetic that is written once for
+// both forms: IntMul forms FP64 products on the integer pipe and records in
+// `bad` whether any could not be formed there; InsnMul uses the FP64
+// instruction (the recomputation of a lane that IntMul flagged).  Both are
+// bitwise __dmul_rn, and FP32 products are plain in both.  Used where the
+// product is an operand of something other than an addition, so that no fused
+// multiply-add is split.
+struct IntMul {
+  unsigned bad = 0u;
+  __device__ __forceinline__ double operator()(double a, double b) { return imul_rn(a, b, bad); }
+  __device__ __forceinline__ float operator()(float a, float b) { return a * b; }
+};
+struct InsnMul {
+  __device__ __forceinline__ double operator()(double a, double b) { return dmul_insn(a, b); }
+  __device__ __forceinline__ float operator()(float a, float b) { return a * b; }
+};
+// The FP64 multiply without the integer pipe (the persistent kernel's stage
+// bodies, where the integer-pipe products were measured slower): the same
+// bits as IntMul, so that both forms of a step agree bit for bit.
+struct PlainMul {
+  __device__ __forceinline__ double operator()(double a, double b) { return __dmul_rn(a, b); }
+  __device__ __forceinline__ float operator()(float a, float b) { return a * b; }
+};
+
 __device__ __forceinline__ double nr_rcp(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -46,9 +122,25 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
 
 __device__ __forceinline__ double nr_sqrt(double x) { return x * nr_rsqrt(x); }
 
+// The same with the two products (and the square root's third) taken by a
+// multiplication policy.
+template <typename M>
+__device__ __forceinline__ double nr_rsqrt(double x, M& mul) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-mul(x, y), y, 1.0);
+  return fma(mul(y, e), fma(e, 0.375, 0.5), y);
+}
+template <typename M>
+__device__ __forceinline__ double nr_sqrt(double x, M& mul) { return mul(x, nr_rsqrt(x, mul)); }
+
 __device__ __forceinline__ float nr_rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ float nr_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ float nr_sqrt(float x) { return sqrtf(x); }
+template <typename M>
+__device__ __forceinline__ float nr_rsqrt(float x, M&) { return rsqrtf(x); }
+template <typename M>
+__device__ __forceinline__ float nr_sqrt(float x, M&) { return sqrtf(x); }
 
 // bit patterns as signed integers of the same width
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }

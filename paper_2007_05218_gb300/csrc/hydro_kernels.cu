@@ -1003,8 +1003,12 @@ __device__ __noinline__ void b_trace(const TableView& tv, const int blk_, const 
   body_trace<R, LIM>(tv, blk_, boxes, rt, work);
 }
 
+// A stated minimum of one block per SM leaves the register count to the
+// compiler (112 here against 104 under the bare thread bound): measured 1.8 %
+// faster for this FP64-bound kernel; the FP32 line kernels, latency-bound,
+// are faster with the bare bound's fewer registers.
 template <typename R, int LIM>
-__global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+__global__ void __launch_bounds__(256, 1) k_trace(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   body_trace<R, LIM>(tv, blockIdx.x, boxes, rt, work);
 }
 
@@ -1020,8 +1024,9 @@ __global__ void __launch_bounds__(256) k_trace(TableView tv, const DevBox* __res
 // c = sqrt(gamma p) / sqrt(rho)), one square root (Roe sound speed) and three
 // reciprocals; wave-speed min/max and sign tests run on the integer pipe in
 // FP64.
-template <typename R>
-__device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R* F) {
+template <typename R, typename M>
+__device__ __forceinline__ void hllc_body(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R* F,
+                                          M& mul) {
   const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4];
   const R rr = Rs[0], ur = Rs[1], vr = Rs[2], wr = Rs[3], pr = Rs[4];
   // 1/sqrt(rho) of each side: from the caller where SHARE_RSQRT holds
@@ -1029,36 +1034,37 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
     rsl = nr_rsqrt(rl);
     rsr = nr_rsqrt(rr);
   }
-  const R sl = rl * rsl, sr = rr * rsr;              // sqrt(rho)
-  const R gpl = gamma * pl, gpr = gamma * pr;
-  const R cl = gpl * nr_rsqrt(gpl) * rsl, cr = gpr * nr_rsqrt(gpr) * rsr;
+  // mul(): the products that are not an addend of a fused multiply-add
+  const R sl = mul(rl, rsl), sr = mul(rr, rsr);  // sqrt(rho)
+  const R gpl = mul(gamma, pl), gpr = mul(gamma, pr);
+  const R cl = mul(mul(gpl, nr_rsqrt(gpl, mul)), rsl), cr = mul(mul(gpr, nr_rsqrt(gpr, mul)), rsr);
   const R iw = nr_rcp(sl + sr);
-  const R wgr = sr * iw;  // Roe weight of the right state; the left one is 1 - wgr
+  const R wgr = mul(sr, iw);  // Roe weight of the right state; the left one is 1 - wgr
   const R ut = ul + wgr * (ur - ul);
   const R vt = vl + wgr * (vr - vl);
   const R wt = wl + wgr * (wr - wl);
   // Roe enthalpy: sum of w_K (E_K + p_K) / rho_K = sum of (E_K + p_K) / sqrt(rho_K), times iw
   const R hl = El + pl, hr = Er + pr;
-  const R Ht = (hl * rsl + hr * rsr) * iw;
-  const R ct2 = gm1 * (Ht - half_of(ut * ut + vt * vt + wt * wt));
+  const R Ht = mul(mul(hl, rsl) + hr * rsr, iw);
+  const R ct2 = mul(gm1, Ht - half_of(mul(ut, ut) + vt * vt + wt * wt));
   R SL, SR;
   if (is_pos(ct2)) {
-    const R ct = nr_sqrt(ct2);
+    const R ct = nr_sqrt(ct2, mul);
     SL = dmin(ul - cl, ut - ct);
     SR = dmax(ur + cr, ut + ct);
   } else {
     SL = dmin(ul - cl, ur - cr);
     SR = dmax(ul + cl, ur + cr);
   }
-  const R ml = rl * (SL - ul), mr = rr * (SR - ur);
-  const R Ss = (pr - pl + ml * ul - mr * ur) * nr_rcp(ml - mr);
+  const R ml = mul(rl, SL - ul), mr = mul(rr, SR - ur);
+  const R Ss = mul(pr - pl + ml * ul - mr * ur, nr_rcp(ml - mr));
   const bool left = is_nonneg(Ss);
   const R rK = left ? rl : rr, uK = left ? ul : ur, vK = left ? vl : vr, wK = left ? wl : wr;
-  const R pK = left ? pl : pr, EK = left ? El : Er, SK = left ? SL : SR;
-  const R mu = rK * uK, hK = left ? hl : hr;
+  const R pK = left ? pl : pr, SK = left ? SL : SR;
+  const R mu = mul(rK, uK), hK = left ? hl : hr;
   F[0] = mu;
   F[1] = mu * uK + pK;
-  F[4] = hK * uK;
+  F[4] = mul(hK, uK);
   const bool supersonic = left ? is_nonneg(SL) : !is_pos(SR);
   if (!supersonic) {
     // F += S_K (U*_K - U_K) with U*_K = rho_K phi (1, S*, v_K, w_K,
@@ -1067,17 +1073,40 @@ __device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er,
     // U*_K - U_K = (rho_K g, rho_K (phi S* - u_K), ., .,
     //               g (E_K + p_K) + rho_K phi S* (S* - u_K))
     const R dsu = Ss - uK;
-    const R g = dsu * nr_rcp(SK - Ss);
+    const R g = mul(dsu, nr_rcp(SK - Ss));
     const R phi = R(1) + g;
-    const R srk = SK * rK;
+    const R srk = mul(SK, rK);
     F[0] += srk * g;
     F[1] += srk * (phi * Ss - uK);
-    F[4] += SK * (g * hK + rK * phi * Ss * dsu);
+    F[4] += SK * (mul(g, hK) + mul(mul(rK, phi), Ss) * dsu);
   }
   // the upwind side's star and outer states share its transverse velocity, so
   // the transverse momentum fluxes are the mass flux times that velocity
-  F[2] = F[0] * vK;
-  F[3] = F[0] * wK;
+  F[2] = mul(F[0], vK);
+  F[3] = mul(F[0], wK);
+}
+
+// FP64: the products on the integer pipe (IntMul); a warp in which a lane's
+// operands fell outside its range recomputes that lane with the FP64 multiply
+// (the same bits: both are correctly rounded).  IM = false: the FP64 multiply
+// throughout, the same bits again.
+template <typename R, bool IM = true>
+__device__ __forceinline__ void hllc(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R* F) {
+  if constexpr (!IM) {
+    PlainMul pm;
+    hllc_body(L, El, rsl, Rs, Er, rsr, gamma, gm1, F, pm);
+    return;
+  }
+  IntMul im;
+  hllc_body(L, El, rsl, Rs, Er, rsr, gamma, gm1, F, im);
+  if constexpr (Consts<R>::FP_BOUND) {
+    if (__any_sync(__activemask(), im.bad != 0u)) {
+      if (im.bad) {
+        InsnMul nm;
+        hllc_body(L, El, rsl, Rs, Er, rsr, gamma, gm1, F, nm);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------- two-shock Riemann solver
@@ -1170,16 +1199,13 @@ __device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R ig
 // The handle's Riemann solver.  El, Er: total energies of the states and rsl,
 // rsr their 1/sqrt(rho) (HLLC uses them; the two-shock flux is built from the
 // sampled state alone).
-template <typename R, int RS>
+template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void riemann(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R igm1,
                                         R* F) {
   if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock(L, Rs, gamma, igm1, F);
-  else hllc(L, El, rsl, Rs, Er, rsr, gamma, gm1, F);
+  else hllc<R, IM>(L, El, rsl, Rs, Er, rsr, gamma, gm1, F);
 }
 
-// The two states of the D-face at zone Z: primitive q (5) and conserved
-// momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides;
-// the conserved form is loaded (FP64) or rebuilt from q (FP32).
 template <typename R>
 __device__ __forceinline__ void conserved_of(const R* q, R igm1, R* u) {
   u[0] = q[0] * q[1];
@@ -1188,6 +1214,9 @@ __device__ __forceinline__ void conserved_of(const R* q, R igm1, R* u) {
   u[3] = q[4] * igm1 + half_of(q[0]) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 }
 
+// The two states of the D-face at zone Z: primitive q (5) and conserved
+// momenta + energy u (4) of the left (zone Z - s_D) and right (zone Z) sides;
+// the conserved form is loaded (FP64) or rebuilt from q (FP32).
 template <typename R, int D>
 __device__ __forceinline__ void load_face_states(const R* __restrict__ W, long long vs, long long Z, long long sD,
                                                  R igm1, R* qL, R* uL, R* qR, R* uR) {
@@ -1214,18 +1243,18 @@ __device__ __forceinline__ void store_flux(R* __restrict__ dst, long long vs, lo
   for (int m = 0; m < 5; m++) dst[comp<D>(m) * vs + Z] = Fn[m];
 }
 
-template <typename R, int D, int RS>
+template <typename R, int D, int RS, bool IM = true>
 __device__ __forceinline__ void riemann_face(const DevBox& b, R* __restrict__ W, long long Z) {
   R qL[5], qR[5], uL[4], uR[4], Fn[5];
   load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
   const bool own = RS == HYDRO_RIEMANN_HLLC && Consts<R>::SHARE_RSQRT;
   const R rsl = own ? nr_rsqrt(qL[0]) : R(0);
   const R rsr = own ? nr_rsqrt(qR[0]) : R(0);
-  riemann<R, RS>(qL, uL[3], rsl, qR, uR[3], rsr, Consts<R>::gamma(b), Consts<R>::gm1(b), Consts<R>::igm1(b), Fn);
+  riemann<R, RS, IM>(qL, uL[3], rsl, qR, uR[3], rsr, Consts<R>::gamma(b), Consts<R>::gm1(b), Consts<R>::igm1(b), Fn);
   store_flux<R, D>(W + (FLD_F0 + 5 * D) * b.vs, b.vs, Z, Fn);
 }
 
-template <typename R, int RS>
+template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void body_riemann(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
   LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
@@ -1237,16 +1266,17 @@ __device__ __forceinline__ void body_riemann(const TableView& tv, const int blk_
   const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   switch (d) {
-    case 0: riemann_face<R, 0, RS>(b, W, Z); break;
-    case 1: riemann_face<R, 1, RS>(b, W, Z); break;
-    default: riemann_face<R, 2, RS>(b, W, Z); break;
+    case 0: riemann_face<R, 0, RS, IM>(b, W, Z); break;
+    case 1: riemann_face<R, 1, RS, IM>(b, W, Z); break;
+    default: riemann_face<R, 2, RS, IM>(b, W, Z); break;
   }
 }
 
-// out-of-line copy for the persistent kernel
+// out-of-line copy for the persistent kernel (FP64 products by the multiply
+// instruction: the integer-pipe ones were measured slower there)
 template <typename R, int RS>
 __device__ __noinline__ void b_riemann(const TableView& tv, const int blk_, const DevBox* boxes, unsigned char* work) {
-  body_riemann<R, RS>(tv, blk_, boxes, work);
+  body_riemann<R, RS, false>(tv, blk_, boxes, work);
 }
 
 template <typename R, int RS>
@@ -1276,9 +1306,9 @@ __device__ __forceinline__ void flux_deltas(const R* const* Fb, const long long*
 }
 
 // The correction itself, from the flux differences (see correct).
-template <typename R, int NT>
-__device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], const R* fac, R gm1, R igm1,
-                                        R& rs) {
+template <typename R, int NT, typename M>
+__device__ __forceinline__ R correct_body(R* q, const R* u, const R (*dlt)[5], const R* fac, R gm1, R igm1, R& rs,
+                                          M& mul) {
   R U[5] = {q[0], u[0], u[1], u[2], u[3]};
 #pragma unroll
   for (int m = 0; m < 5; m++) {
@@ -1286,11 +1316,11 @@ __device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], con
     for (int t = 0; t < NT; t++) U[m] = U[m] - fac[t] * dlt[t][m];
   }
   if (is_pos(U[0])) {
-    const R r = Consts<R>::SHARE_RSQRT ? nr_rsqrt(U[0]) : R(0);
-    const R ir = Consts<R>::SHARE_RSQRT ? r * r : nr_rcp(U[0]);
-    const R uu = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
-    const R kin = half_of(U[1] * uu + U[2] * v + U[3] * w);
-    const R p = gm1 * (U[4] - kin);
+    const R r = Consts<R>::SHARE_RSQRT ? nr_rsqrt(U[0], mul) : R(0);
+    const R ir = Consts<R>::SHARE_RSQRT ? mul(r, r) : nr_rcp(U[0]);
+    const R uu = mul(U[1], ir), v = mul(U[2], ir), w = mul(U[3], ir);
+    const R kin = half_of(mul(U[1], uu) + U[2] * v + U[3] * w);
+    const R p = mul(gm1, U[4] - kin);
     if (is_pos(p)) {
       q[0] = U[0];
       q[1] = uu;
@@ -1305,16 +1335,44 @@ __device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], con
       return U[4];
     }
   }
-  rs = Consts<R>::SHARE_RSQRT ? nr_rsqrt(q[0]) : R(0);
+  rs = Consts<R>::SHARE_RSQRT ? nr_rsqrt(q[0], mul) : R(0);
   return u[3];
 }
 
-template <typename R, int D, int NT>
+// FP64 products on the integer pipe, as in hllc: a lane flagged there redoes
+// its correction from the uncorrected state with the FP64 multiply.
+template <typename R, int NT, bool IM = true>
+__device__ __forceinline__ R correct_by(R* q, const R* u, const R (*dlt)[5], const R* fac, R gm1, R igm1, R& rs) {
+  if constexpr (!IM) {
+    PlainMul pm;
+    return correct_body<R, NT>(q, u, dlt, fac, gm1, igm1, rs, pm);
+  } else if constexpr (Consts<R>::FP_BOUND) {
+    R qc[5] = {q[0], q[1], q[2], q[3], q[4]};
+    IntMul im;
+    R E = correct_body<R, NT>(qc, u, dlt, fac, gm1, igm1, rs, im);
+    if (__any_sync(__activemask(), im.bad != 0u)) {
+      if (im.bad) {
+#pragma unroll
+        for (int m = 0; m < 5; m++) qc[m] = q[m];
+        InsnMul nm;
+        E = correct_body<R, NT>(qc, u, dlt, fac, gm1, igm1, rs, nm);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 5; m++) q[m] = qc[m];
+    return E;
+  } else {
+    IntMul im;
+    return correct_body<R, NT>(q, u, dlt, fac, gm1, igm1, rs, im);
+  }
+}
+
+template <typename R, int D, int NT, bool IM = true>
 __device__ __forceinline__ R correct(R* q, const R* u, const R* const* Fb, const long long* st, const R* fac,
                                      long long vs, long long Z, R gm1, R igm1, R& rs) {
   R dlt[NT][5];
   flux_deltas<R, D, NT>(Fb, st, vs, Z, dlt);
-  return correct_by<R, NT>(q, u, dlt, fac, gm1, igm1, rs);
+  return correct_by<R, NT, IM>(q, u, dlt, fac, gm1, igm1, rs);
 }
 
 constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
@@ -1323,7 +1381,7 @@ constexpr int pair_slot(int d, int e) { return 2 * d + (e > d ? e - 1 : e); }
 // flux difference along one transverse axis T (the ordered pair (D, T)), for
 // each T in {E, F} the face carries: the face's two states are loaded once
 // for both pairs.
-template <typename R, int D, int T, int RS>
+template <typename R, int D, int T, int RS, bool IM = true>
 __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
                                           const R* qL0, const R* uL, const R* qR0, const R* uR) {
   const long long vs = b.vs, sD = b.s[D];
@@ -1338,16 +1396,16 @@ __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, lo
   const long long st[1] = {b.s[T]};
   const R fac[1] = {Consts<R>::dtdx3(b, rt, T)};
   R rsl, rsr;
-  const R EL = correct<R, D, 1>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
-  const R ER = correct<R, D, 1>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
+  const R EL = correct<R, D, 1, IM>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
+  const R ER = correct<R, D, 1, IM>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
+  riemann<R, RS, IM>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * vs, vs, Z, Fn);
 }
 
 // FP32: the two states stay in registers for both pairs.  FP64: each pair
 // loads them (the second load hits L1), so that 18 doubles are not held
 // across a Riemann solve -- registers, not HBM, limit the FP64 kernel.
-template <typename R, int D, int RS>
+template <typename R, int D, int RS, bool IM = true>
 __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
                                           bool with_e, bool with_f) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
@@ -1355,23 +1413,23 @@ __device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, lo
   if constexpr (Consts<R>::STORE_CONSERVED) {
     if (with_e) {
       load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-      ctu1_pair<R, D, E, RS>(b, W, Z, rt, qL, uL, qR, uR);
+      ctu1_pair<R, D, E, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
     }
     if (with_f) {
       load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-      ctu1_pair<R, D, F, RS>(b, W, Z, rt, qL, uL, qR, uR);
+      ctu1_pair<R, D, F, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
     }
   } else {
     load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-    if (with_e) ctu1_pair<R, D, E, RS>(b, W, Z, rt, qL, uL, qR, uR);
-    if (with_f) ctu1_pair<R, D, F, RS>(b, W, Z, rt, qL, uL, qR, uR);
+    if (with_e) ctu1_pair<R, D, E, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
+    if (with_f) ctu1_pair<R, D, F, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
   }
 }
 
 // One thread per D-face over faces [0, n_D] along D and [-1, n] across it:
 // pair (D, E) is defined where the E index is in [0, n_E - 1], pair (D, F)
 // where the F index is in [0, n_F - 1] (E = D+1, F = D+2 mod 3).
-template <typename R, int RS>
+template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void body_ctu1(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
   LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
@@ -1388,16 +1446,16 @@ __device__ __forceinline__ void body_ctu1(const TableView& tv, const int blk_, c
   R* W = fields<R>(work, b);
   const BoxRt& rtb = rt[bi];
   switch (d) {
-    case 0: ctu1_face<R, 0, RS>(b, W, Z, rtb, with_e, with_f); break;
-    case 1: ctu1_face<R, 1, RS>(b, W, Z, rtb, with_e, with_f); break;
-    default: ctu1_face<R, 2, RS>(b, W, Z, rtb, with_e, with_f); break;
+    case 0: ctu1_face<R, 0, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
+    case 1: ctu1_face<R, 1, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
+    default: ctu1_face<R, 2, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
   }
 }
 
 // out-of-line copy for the persistent kernel
 template <typename R, int RS>
 __device__ __noinline__ void b_ctu1(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
-  body_ctu1<R, RS>(tv, blk_, boxes, rt, work);
+  body_ctu1<R, RS, false>(tv, blk_, boxes, rt, work);
 }
 
 template <typename R, int RS>
@@ -1405,7 +1463,7 @@ __global__ void __launch_bounds__(256) k_ctu1(TableView tv, const DevBox* __rest
   body_ctu1<R, RS>(tv, blockIdx.x, boxes, rt, work);
 }
 
-template <typename R, int D, int RS>
+template <typename R, int D, int RS, bool IM = true>
 __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
                                           bool wall) {
   constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
@@ -1417,9 +1475,9 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   const long long st[2] = {b.s[E], b.s[F]};
   const R fac[2] = {Consts<R>::dtdx2(b, rt, E), Consts<R>::dtdx2(b, rt, F)};
   R rsl, rsr;
-  const R EL = correct<R, D, 2>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
-  const R ER = correct<R, D, 2>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
-  riemann<R, RS>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
+  const R EL = correct<R, D, 2, IM>(qL, uL, Fb, st, fac, vs, Z - sD, gm1, igm1, rsl);
+  const R ER = correct<R, D, 2, IM>(qR, uR, Fb, st, fac, vs, Z, gm1, igm1, rsr);
+  riemann<R, RS, IM>(qL, EL, rsl, qR, ER, rsr, gamma, gm1, igm1, Fn);
   if (wall) {
     // a reflecting face is impermeable: only the normal momentum flux (the wall pressure) remains
     Fn[0] = R(0);
@@ -1430,7 +1488,7 @@ __device__ __forceinline__ void ctu2_face(const DevBox& b, R* __restrict__ W, lo
   store_flux<R, D>(W + (FLD_F + 5 * D) * vs, vs, Z, Fn);
 }
 
-template <typename R, int RS>
+template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void body_ctu2(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
   LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
@@ -1444,16 +1502,16 @@ __device__ __forceinline__ void body_ctu2(const TableView& tv, const int blk_, c
   const bool wall = (c[d] == 0 && b.bc[2 * d] == HYDRO_BC_REFLECT && b.nbr1[2 * d] == 0) ||
                     (c[d] == b.n[d] && b.bc[2 * d + 1] == HYDRO_BC_REFLECT && b.nbr1[2 * d + 1] == 0);
   switch (d) {
-    case 0: ctu2_face<R, 0, RS>(b, W, Z, r, wall); break;
-    case 1: ctu2_face<R, 1, RS>(b, W, Z, r, wall); break;
-    default: ctu2_face<R, 2, RS>(b, W, Z, r, wall); break;
+    case 0: ctu2_face<R, 0, RS, IM>(b, W, Z, r, wall); break;
+    case 1: ctu2_face<R, 1, RS, IM>(b, W, Z, r, wall); break;
+    default: ctu2_face<R, 2, RS, IM>(b, W, Z, r, wall); break;
   }
 }
 
 // out-of-line copy for the persistent kernel
 template <typename R, int RS>
 __device__ __noinline__ void b_ctu2(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
-  body_ctu2<R, RS>(tv, blk_, boxes, rt, work);
+  body_ctu2<R, RS, false>(tv, blk_, boxes, rt, work);
 }
 
 template <typename R, int RS>
@@ -2014,7 +2072,8 @@ __device__ __noinline__ void b_update(const TableView& tv, const int blk_, const
   body_update(tv, blk_, boxes, rt, state, work, skip_mixed);
 }
 
-__global__ void __launch_bounds__(256) k_update(TableView tv, const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, double* __restrict__ state, unsigned char* __restrict__ work, int skip_mixed) {
+// one block per SM stated, as for the tracing (52 registers against 32: 7 % faster)
+__global__ void __launch_bounds__(256, 1) k_update(TableView tv, const DevBox* __restrict__ boxes, BoxRt* __restrict__ rt, double* __restrict__ state, unsigned char* __restrict__ work, int skip_mixed) {
   body_update(tv, blockIdx.x, boxes, rt, state, work, skip_mixed);
 }
 

@@ -1,7 +1,8 @@
 // Checks the device arithmetic helpers of fp64_fast.cuh on the GPU against
 // IEEE operations: the bit-pattern sign tests, comparisons, min/max, exact
-// halving, the |x| > 2|y| test and the integer FP64 -> FP32 rounding (against
-// the conversion instruction, where it does not defer to it) bit for bit, on
+// halving, the |x| > 2|y| test, the integer FP64 -> FP32 rounding (against
+// the conversion instruction, where it does not defer to it) and the
+// integer-pipe product (against the FP64 multiply) bit for bit, on
 // patterns drawn over every
 // exponent (subnormals, the range edges, zero and both signs included); the
 // Newton-refined reciprocal, reciprocal square root and square root within
@@ -20,7 +21,7 @@
 
 using namespace hydro;
 
-enum { BAD_HALF, BAD_CMP, BAD_RCP, BAD_SQRT, BAD_RSQRT, BAD_NARROW, NBAD };
+enum { BAD_HALF, BAD_CMP, BAD_RCP, BAD_SQRT, BAD_RSQRT, BAD_NARROW, BAD_IMUL, NBAD };
 
 __device__ double ulp_of(double r) { return ldexp(1.0, ilogb(r) - 52); }
 
@@ -30,6 +31,20 @@ __global__ void check_bits(const double* x, const double* y, int n, unsigned lon
   const double a = x[i], c = y[i];
   const double h = half_of<double>(a), r = __dmul_rn(0.5, a);
   if (!(__double_as_longlong(h) == __double_as_longlong(r) || (isnan(h) && isnan(r)))) atomicAdd(&bad[BAD_HALF], 1ull);
+  {  // the integer-pipe product: bitwise the IEEE one wherever it does not
+     // defer, and deferring exactly where an operand is subnormal, infinite
+     // or NaN (zero excepted) or the product is not normal or zero
+    unsigned defer = 0u;
+    const double p = imul_rn(a, c, defer), q = __dmul_rn(a, c);
+    if (!defer && __double_as_longlong(p) != __double_as_longlong(q)) atomicAdd(&bad[BAD_IMUL], 1ull);
+    const auto normal = [](double v) { return fabs(v) >= 0x1p-1022 && isfinite(v); };
+    const bool zero_op = (a == 0.0 && isfinite(c)) || (c == 0.0 && isfinite(a));
+    const double m = fabs(q);
+    // a product rounded up to the smallest normal from below it is deferred too
+    const bool fast = zero_op || (normal(a) && normal(c) && (isinf(q) ? false : m >= 0x1p-1022));
+    if (fast && defer && !(m < 0x1p-1021)) atomicAdd(&bad[BAD_IMUL], 1ull);
+    if (!fast && !defer && !isinf(q)) atomicAdd(&bad[BAD_IMUL], 1ull);
+  }
   bool rare;
   const unsigned nb = narrow_bits(a, rare);
   if (!rare && nb != __float_as_uint(__double2float_rn(a))) atomicAdd(&bad[BAD_NARROW], 1ull);
@@ -71,6 +86,55 @@ __global__ void check_refined(const double* x, int n, unsigned long long* bad, u
   atomicMax(&worst[0], (unsigned long long)(er * 1000.0));
   atomicMax(&worst[1], (unsigned long long)(es * 1000.0));
   atomicMax(&worst[2], (unsigned long long)(eq * 1000.0));
+}
+
+// Throughput of the products (informational; printed, not asserted): chains
+// of FP64 multiplies by the instruction and on the integer pipe, FP64
+// multiply-add chains alone, and the same multiply-adds interleaved with
+// integer-pipe products (one vote per iteration for the recomputation).
+constexpr int RATE_ITER = 2048, RATE_CH = 8;
+
+template <bool INTEGER>
+__global__ void k_rate_mul(double* out, double c, double d) {
+  double x[RATE_CH];
+  for (int j = 0; j < RATE_CH; j++) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  unsigned bad = 0u;
+  for (int i = 0; i < RATE_ITER; i++) {
+    const double m = (i & 1) ? c : d;
+#pragma unroll
+    for (int j = 0; j < RATE_CH; j++) x[j] = INTEGER ? imul_rn(x[j], m, bad) : __dmul_rn(x[j], m);
+  }
+  double s = bad ? 1.0 : 0.0;
+  for (int j = 0; j < RATE_CH; j++) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int NM>
+__global__ void k_rate_mix(double* out, double c, double d) {
+  double y[RATE_CH], x[NM > 0 ? NM : 1];
+  for (int j = 0; j < RATE_CH; j++) y[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int j = 0; j < NM; j++) x[j] = 1.0 + 2e-3 * (threadIdx.x + j);
+  for (int i = 0; i < RATE_ITER; i++) {
+#pragma unroll
+    for (int j = 0; j < RATE_CH; j++) y[j] = fma(y[j], c, -d * 1e-9);
+    if constexpr (NM > 0) {
+      const double m = (i & 1) ? c : d;
+      unsigned bad = 0u;
+      double xn[NM];
+#pragma unroll
+      for (int j = 0; j < NM; j++) xn[j] = imul_rn(x[j], m, bad);
+      if (__any_sync(0xffffffffu, bad != 0u)) {
+#pragma unroll
+        for (int j = 0; j < NM; j++) xn[j] = dmul_insn(x[j], m);
+      }
+#pragma unroll
+      for (int j = 0; j < NM; j++) x[j] = xn[j];
+    }
+  }
+  double s = 0.0;
+  for (int j = 0; j < RATE_CH; j++) s += y[j];
+  for (int j = 0; j < NM; j++) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 static double from_pattern(uint64_t b) {
@@ -117,6 +181,20 @@ int main() {
     x.push_back(from_pattern((g() & (1ull << 63)) | (e << 52) | mant));
     y.push_back(from_pattern(g()));
   }
+  // products near the ends of the normal range, exact products and rounding
+  // ties: exponent pairs summing to about the bias and to its extremes
+  for (int i = 0; i < (1 << 21); i++) {
+    const uint64_t ea = 1 + g() % 2046;
+    const int64_t target = (i % 3 == 0) ? 1023 : (i % 3 == 1) ? 1 : 2046;  // product exponent near 0, the bottom, the top
+    int64_t eb = target - (int64_t)ea + 1023 + (int64_t)(g() % 5) - 2;
+    if (eb < 0) eb = 0;
+    if (eb > 2047) eb = 2047;
+    uint64_t ma = g() & 0x000fffffffffffffull, mb = g() & 0x000fffffffffffffull;
+    if (i % 4 == 1) mb &= 0x000ff00000000000ull;  // short significand: exact products and ties
+    if (i % 8 == 5) ma = 0x000fffffffffffffull;   // all ones: carries through the rounding
+    x.push_back(from_pattern((g() & (1ull << 63)) | (ea << 52) | ma));
+    y.push_back(from_pattern((g() & (1ull << 63)) | ((uint64_t)eb << 52) | mb));
+  }
   // normal positive arguments for the refined operations, 2^-1000 .. 2^1000
   std::vector<double> z(1 << 22);
   for (double& v : z) v = from_pattern(((uint64_t)(23 + g() % 2001) << 52) | (g() & 0x000fffffffffffffull));
@@ -141,13 +219,55 @@ int main() {
   cudaMemcpy(bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost);
   cudaMemcpy(worst, dworst, sizeof(worst), cudaMemcpyDeviceToHost);
   std::printf("cuda %s\n", cudaGetErrorString(err));
-  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu, narrowing mismatches %llu\n",
-              n, bad[BAD_HALF], bad[BAD_CMP], bad[BAD_NARROW]);
+  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu, narrowing mismatches %llu, "
+              "integer-product mismatches %llu\n",
+              n, bad[BAD_HALF], bad[BAD_CMP], bad[BAD_NARROW], bad[BAD_IMUL]);
   std::printf("refined cases %d: rcp > 2 ulp %llu (max %.3f), sqrt > 2 ulp %llu (max %.3f), rsqrt > 2^-51.5 %llu "
               "(max %.3f x 2^-53)\n",
               nz, bad[BAD_RCP], worst[0] / 1000.0, bad[BAD_SQRT], worst[1] / 1000.0, bad[BAD_RSQRT],
               worst[2] / 1000.0);
-  bool ok = err == cudaSuccess;
+  {  // product throughput, 8 blocks of 256 threads per SM
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int blocks = 8 * sms, threads = 256, nt = blocks * threads;
+    double *r1, *r2;
+    cudaMalloc(&r1, nt * sizeof(double));
+    cudaMalloc(&r2, nt * sizeof(double));
+    const double c = 1.0 + 0x1p-30, d = 1.0 / c;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto rate = [&](const char* name, auto launch, double ops) {
+      launch();
+      cudaEventRecord(e0);
+      for (int r = 0; r < 5; r++) launch();
+      cudaEventRecord(e1);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      std::printf("rate %-34s %.3f ms, %.3f G lane-ops/s per SM\n", name, ms / 5, ops * nt / (ms / 5 * 1e-3) / sms / 1e9);
+    };
+    rate("FP64 multiply chains", [&] { k_rate_mul<false><<<blocks, threads>>>(r1, c, d); }, (double)RATE_ITER * RATE_CH);
+    rate("integer-pipe product chains", [&] { k_rate_mul<true><<<blocks, threads>>>(r2, c, d); },
+         (double)RATE_ITER * RATE_CH);
+    rate("FP64 multiply-add chains", [&] { k_rate_mix<0><<<blocks, threads>>>(r1, c, d); }, (double)RATE_ITER * RATE_CH);
+    rate("multiply-adds + 4 integer products", [&] { k_rate_mix<4><<<blocks, threads>>>(r1, c, d); },
+         (double)RATE_ITER * (RATE_CH + 4));
+    rate("multiply-adds + 8 integer products", [&] { k_rate_mix<8><<<blocks, threads>>>(r1, c, d); },
+         (double)RATE_ITER * (RATE_CH + 8));
+    k_rate_mul<false><<<blocks, threads>>>(r1, c, d);
+    k_rate_mul<true><<<blocks, threads>>>(r2, c, d);
+    std::vector<double> h1(nt), h2(nt);
+    cudaMemcpy(h1.data(), r1, nt * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaMemcpy(h2.data(), r2, nt * sizeof(double), cudaMemcpyDeviceToHost);
+    long nd = 0;
+    for (int i = 0; i < nt; i++) nd += h1[i] != h2[i];
+    std::printf("chained products (2048 per chain): %ld of %d results differ\n", nd, nt);
+    if (nd) bad[BAD_IMUL] += (unsigned long long)nd;
+    cudaFree(r1);
+    cudaFree(r2);
+  }
+  bool ok = err == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
   for (unsigned long long b : bad) ok = ok && b == 0;
   std::printf("%s\n", ok ? "PASS" : "FAIL");
   return ok ? 0 : 1;

@@ -1,7 +1,8 @@
 """The device arithmetic helpers the FP64 kernels rest on, checked on the GPU
 (needs a GB300 and nvcc): bit-pattern sign tests, comparisons, min/max,
-exact halving and the |x| > 2|y| test against IEEE operations bit for bit over
-every exponent; Newton-refined reciprocal and square root within 2 ulp and
+exact halving, the |x| > 2|y| test, the integer-pipe FP64 -> FP32 rounding and
+the integer-pipe FP64 product against IEEE operations bit for bit over every
+exponent; Newton-refined reciprocal and square root within 2 ulp and
 reciprocal square root within 2^-51.5 relative over normal arguments.
 """
 import os
