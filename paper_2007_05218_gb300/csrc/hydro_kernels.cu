@@ -815,6 +815,16 @@ __device__ __forceinline__ void parabola(R am1, R a0, R ap1, R dm1, R d0, R dp1,
   cw84_limit<R, BLEND>(a0, f, L, Rt);
 }
 
+// Conserved momenta (normal frame) and total energy of an edge state q, the
+// products taken by a multiplication policy.
+template <typename R, typename M>
+__device__ __forceinline__ void conserved_m(const R* q, R igm1, R* u, M& mul) {
+  u[0] = mul(q[0], q[1]);
+  u[1] = mul(q[0], q[2]);
+  u[2] = mul(q[0], q[3]);
+  u[3] = mul(q[4], igm1) + half_of(q[0]) * (mul(q[1], q[1]) + q[2] * q[2] + q[3] * q[3]);
+}
+
 // Conserved momenta (normal frame) and total energy of a traced edge state,
 // stored once so that the Riemann and CTU stages need not rebuild them.
 template <typename R, int D>
@@ -828,105 +838,122 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
 
 // Characteristic tracing of one zone along one axis (Miller & Colella 2002
 // style, R4): zone values a0, limited parabola edges aL, aR of the five
-// normal-frame variables, zone sound speed cs with ic = 1/c and cr = c/rho,
-// dt/dx.  Hands the right-edge state (side 1, the left state of the zone's
-// high face) and then the left-edge state (side 0) to sink(side, q[5]) as
-// soon as each is formed.
-template <typename R, typename Sink>
-__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R ic, R cr, R dtdx,
-                                            Sink&& sink) {
-  // The parabola's dA = aR - aL and a6 = 6 (a0 - (aL + aR)/2) (CW84 §1); the
-  // factor 6 of a6 is carried by h2 below, so c6 holds a6 / 6.  For a wave
-  // of speed lambda, sigma = |lambda| dt/dx, the average of the parabola over
-  // the wave's domain of dependence at an edge is edge -+ h1 (dA -+ h2 c6)
-  // with h1 = sigma / 2 and h2 = 6 (1 - 2 sigma / 3) = 6 - 4 sigma.
-  R dA[5], c6[5];
+// normal-frame variables (and their dA = aR - aL, c6), zone sound speed cs
+// with ic = 1/c and cr = c/rho, dt/dx.  trace_side<1> forms the right-edge
+// state (the left state of the zone's high face), trace_side<0> the
+// left-edge state, with the products that are not an addend of a fused
+// multiply-add taken by a multiplication policy.
+//
+// The parabola's dA = aR - aL and a6 = 6 (a0 - (aL + aR)/2) (CW84 §1); the
+// factor 6 of a6 is carried by h2 below, so c6 holds a6 / 6.  For a wave of
+// speed lambda, sigma = |lambda| dt/dx, the average of the parabola over the
+// wave's domain of dependence at an edge is edge -+ h1 (dA -+ h2 c6) with
+// h1 = sigma / 2 and h2 = 6 (1 - 2 sigma / 3) = 6 - 4 sigma.
+template <typename R>
+__device__ __forceinline__ void parabola_coeffs(const R* a0, const R* aL, const R* aR, R* dA, R* c6) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     dA[m] = aR[m] - aL[m];
     c6[m] = a0[m] - half_of(aL[m] + aR[m]);
   }
+}
+
+template <int SIDE, typename R, typename M>
+__device__ __forceinline__ void trace_side(const R* a0, const R* aL, const R* aR, const R* dA, const R* c6, R cs, R ic,
+                                           R cr, R dtdx, R* out, M& mul) {
   const R rho = a0[0], u = a0[1];
-  const R rc = rho * half_of(ic);   // rho / 2c
-  const R ic2 = ic * ic;            // 1 / c^2
-  const R i2c2 = half_of(ic2);      // 1 / 2c^2
-  const R c2 = cs * cs;
+  const R rc = mul(rho, half_of(ic));  // rho / 2c
+  const R ic2 = mul(ic, ic);           // 1 / c^2
+  const R i2c2 = half_of(ic2);         // 1 / 2c^2
+  const R c2 = mul(cs, cs);
   const R lm = u - cs, lp = u + cs;
-  const R hdt = half_of(dtdx), fdt = R(4) * dtdx;
-
-  R out[5];
-  // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
-  if (is_pos(lp)) {
-    R h1 = lp * hdt, h2 = R(6) - lp * fdt;
-    R ref[5];
+  const R hdt = half_of(dtdx), fdt = mul(R(4), dtdx);
+  if constexpr (SIDE == 1) {
+    // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
+    if (is_pos(lp)) {
+      R h1 = mul(lp, hdt), h2 = R(6) - lp * fdt;
+      R ref[5];
 #pragma unroll
-    for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * c6[m]);
-    R bm = R(0), b0 = R(0);
-    out[2] = ref[2];
-    out[3] = ref[3];
-    const bool wm = is_pos(lm), w0 = is_pos(u);
-    if (any_in_warp<R>(wm)) {
-      h1 = lm * hdt; h2 = R(6) - lm * fdt;
-      const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * c6[1]));
-      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
-      if (wm) bm = -rc * du + i2c2 * dp;
-    }
-    if (any_in_warp<R>(w0)) {
-      h1 = u * hdt; h2 = R(6) - u * fdt;
-      const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * c6[0]));
-      const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
-      if (w0) {
-        b0 = dr - ic2 * dp;
-        out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
-        out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
+      for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * c6[m]);
+      R bm = R(0), b0 = R(0);
+      out[2] = ref[2];
+      out[3] = ref[3];
+      const bool wm = is_pos(lm), w0 = is_pos(u);
+      if (any_in_warp<R>(wm)) {
+        h1 = mul(lm, hdt); h2 = R(6) - lm * fdt;
+        const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * c6[1]));
+        const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
+        if (wm) bm = mul(-rc, du) + i2c2 * dp;
       }
-    }
-    out[0] = ref[0] - (bm + b0);
-    out[1] = ref[1] + cr * bm;
-    out[4] = ref[4] - c2 * bm;
-  } else {
+      if (any_in_warp<R>(w0)) {
+        h1 = mul(u, hdt); h2 = R(6) - u * fdt;
+        const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * c6[0]));
+        const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
+        if (w0) {
+          b0 = dr - ic2 * dp;
+          out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
+          out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
+        }
+      }
+      out[0] = ref[0] - (bm + b0);
+      out[1] = ref[1] + cr * bm;
+      out[4] = ref[4] - c2 * bm;
+    } else {
 #pragma unroll
-    for (int m = 0; m < 5; m++) out[m] = a0[m];
+      for (int m = 0; m < 5; m++) out[m] = a0[m];
+    }
+    if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
+    if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
+  } else {
+    // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
+    if (is_neg(lm)) {
+      R h1 = mul(-lm, hdt), h2 = R(6) + lm * fdt;
+      R ref[5];
+#pragma unroll
+      for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * c6[m]);
+      R bp = R(0), b0 = R(0);
+      out[2] = ref[2];
+      out[3] = ref[3];
+      const bool wp = is_neg(lp), w0 = is_neg(u);
+      if (any_in_warp<R>(wp)) {
+        h1 = mul(-lp, hdt); h2 = R(6) + lp * fdt;
+        const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * c6[1]));
+        const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
+        if (wp) bp = mul(rc, du) + i2c2 * dp;
+      }
+      if (any_in_warp<R>(w0)) {
+        h1 = mul(-u, hdt); h2 = R(6) + u * fdt;
+        const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * c6[0]));
+        const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
+        if (w0) {
+          b0 = dr - ic2 * dp;
+          out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
+          out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
+        }
+      }
+      out[0] = ref[0] - (b0 + bp);
+      out[1] = ref[1] - cr * bp;
+      out[4] = ref[4] - c2 * bp;
+    } else {
+#pragma unroll
+      for (int m = 0; m < 5; m++) out[m] = a0[m];
+    }
+    if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
+    if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
   }
-  if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
-  if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
+}
+
+// Both edge states in turn, handed to sink(side, q[5]) as soon as each is
+// formed (plain products: the FP32 kernels and the form that forms 1/c here).
+template <typename R, typename Sink>
+__device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* aR, R cs, R ic, R cr, R dtdx,
+                                            Sink&& sink) {
+  R dA[5], c6[5], out[5];
+  parabola_coeffs(a0, aL, aR, dA, c6);
+  PlainMul pm;
+  trace_side<1>(a0, aL, aR, dA, c6, cs, ic, cr, dtdx, out, pm);
   sink(1, out);
-
-  // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
-  if (is_neg(lm)) {
-    R h1 = -lm * hdt, h2 = R(6) + lm * fdt;
-    R ref[5];
-#pragma unroll
-    for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * c6[m]);
-    R bp = R(0), b0 = R(0);
-    out[2] = ref[2];
-    out[3] = ref[3];
-    const bool wp = is_neg(lp), w0 = is_neg(u);
-    if (any_in_warp<R>(wp)) {
-      h1 = -lp * hdt; h2 = R(6) + lp * fdt;
-      const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * c6[1]));
-      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
-      if (wp) bp = rc * du + i2c2 * dp;
-    }
-    if (any_in_warp<R>(w0)) {
-      h1 = -u * hdt; h2 = R(6) + u * fdt;
-      const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * c6[0]));
-      const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
-      if (w0) {
-        b0 = dr - ic2 * dp;
-        out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
-        out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
-      }
-    }
-    out[0] = ref[0] - (b0 + bp);
-    out[1] = ref[1] - cr * bp;
-    out[4] = ref[4] - c2 * bp;
-  } else {
-#pragma unroll
-    for (int m = 0; m < 5; m++) out[m] = a0[m];
-  }
-  if (dgt(R(SMALL_DENS), out[0])) out[0] = R(SMALL_DENS);
-  if (dgt(R(SMALL_PRES), out[4])) out[4] = R(SMALL_PRES);
+  trace_side<0>(a0, aL, aR, dA, c6, cs, ic, cr, dtdx, out, pm);
   sink(0, out);
 }
 
@@ -956,7 +983,37 @@ __device__ __forceinline__ void zone_parabolas(const R* __restrict__ W, long lon
   }
 }
 
-template <typename R, int D, int LIM>
+// One FP64 edge state of a zone along D (and its conserved form) formed with
+// integer-pipe products, recomputed with the FP64 multiply in a lane that
+// flagged, and stored.
+template <int SIDE, bool IM, typename R>
+__device__ __forceinline__ void trace_store_side(R* __restrict__ W, long long vs, long long Z, int D, const R* a0,
+                                                 const R* aL, const R* aR, const R* dA, const R* c6, R cs, R ic, R cr,
+                                                 R dtdx, R igm1) {
+  R out[5], u[4];
+  IntMul im;
+  if constexpr (IM) {
+    trace_side<SIDE>(a0, aL, aR, dA, c6, cs, ic, cr, dtdx, out, im);
+    conserved_m(out, igm1, u, im);
+  } else {  // the FP64 multiply throughout (the same bits)
+    PlainMul pm;
+    trace_side<SIDE>(a0, aL, aR, dA, c6, cs, ic, cr, dtdx, out, pm);
+    conserved_m(out, igm1, u, pm);
+  }
+  if (IM && __any_sync(__activemask(), im.bad != 0u)) {
+    if (im.bad) {
+      InsnMul nm;
+      trace_side<SIDE>(a0, aL, aR, dA, c6, cs, ic, cr, dtdx, out, nm);
+      conserved_m(out, igm1, u, nm);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 5; m++) W[((SIDE ? FLD_QP : FLD_QM) + 5 * D + m) * vs + Z] = out[m];
+#pragma unroll
+  for (int j = 0; j < 4; j++) W[((SIDE ? FLD_UP : FLD_UM) + 4 * D + j) * vs + Z] = u[j];
+}
+
+template <typename R, int D, int LIM, bool IM = true>
 __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, long long Z, R dtdx) {
   const long long vs = b.vs, s = b.s[D];
   const R igm1 = Consts<R>::igm1(b);
@@ -975,13 +1032,22 @@ __device__ __forceinline__ void trace_zone(const DevBox& b, R* __restrict__ W, l
     for (int m = 0; m < 5; m++) W[((side ? FLD_QP : FLD_QM) + 5 * D + m) * vs + Z] = out[m];
     if constexpr (Consts<R>::STORE_CONSERVED) store_conserved<R, D>(W, vs, Z, side ? FLD_UP : FLD_UM, out, igm1);
   };
-  if constexpr (Consts<R>::PRIM_RECIPROCALS)
-    trace_edges(a0, aL, aR, cs, W[FLD_IC * vs + Z], W[FLD_CR * vs + Z], dtdx, sink);
-  else
+  if constexpr (Consts<R>::PRIM_RECIPROCALS) {
+    // FP64: each edge state and its conserved form with the products on the
+    // integer pipe; a warp with a flagged lane redoes that side with the FP64
+    // multiply (the same bits) before it is stored (IM = false: the FP64
+    // multiply throughout, the persistent kernel's bodies)
+    const R ic = W[FLD_IC * vs + Z], cr = W[FLD_CR * vs + Z];
+    R dA[5], c6[5];
+    parabola_coeffs(a0, aL, aR, dA, c6);
+    trace_store_side<1, IM>(W, vs, Z, D, a0, aL, aR, dA, c6, cs, ic, cr, dtdx, igm1);
+    trace_store_side<0, IM>(W, vs, Z, D, a0, aL, aR, dA, c6, cs, ic, cr, dtdx, igm1);
+  } else {
     trace_edges(a0, aL, aR, cs, dtdx, sink);
+  }
 }
 
-template <typename R, int LIM>
+template <typename R, int LIM, bool IM = true>
 __device__ __forceinline__ void body_trace(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
   LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
@@ -991,24 +1057,24 @@ __device__ __forceinline__ void body_trace(const TableView& tv, const int blk_, 
   R* W = fields<R>(work, b);
   const BoxRt& r = rt[bi];
   switch (z_) {
-    case 0: trace_zone<R, 0, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 0)); break;
-    case 1: trace_zone<R, 1, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
-    default: trace_zone<R, 2, LIM>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
+    case 0: trace_zone<R, 0, LIM, IM>(b, W, Z, Consts<R>::dtdx(b, r, 0)); break;
+    case 1: trace_zone<R, 1, LIM, IM>(b, W, Z, Consts<R>::dtdx(b, r, 1)); break;
+    default: trace_zone<R, 2, LIM, IM>(b, W, Z, Consts<R>::dtdx(b, r, 2)); break;
   }
 }
 
-// out-of-line copy for the persistent kernel
+// out-of-line copy for the persistent kernel (FP64 multiply instruction)
 template <typename R, int LIM>
 __device__ __noinline__ void b_trace(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
-  body_trace<R, LIM>(tv, blk_, boxes, rt, work);
+  body_trace<R, LIM, false>(tv, blk_, boxes, rt, work);
 }
 
-// A stated minimum of one block per SM leaves the register count to the
-// compiler (112 here against 104 under the bare thread bound): measured 1.8 %
-// faster for this FP64-bound kernel; the FP32 line kernels, latency-bound,
-// are faster with the bare bound's fewer registers.
+// Registers capped at 128 (4 blocks of 128 threads per SM): the integer-pipe
+// products of the FP64 tracing want 154, and with that many the kernel was
+// measured 8 % slower (12.29 against 11.28 ms at 256^3; 112 registers: 11.45).
 template <typename R, int LIM>
-__global__ void __launch_bounds__(256, 1) k_trace(TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
+__global__ void __maxnreg__(128) k_trace(
+    TableView tv, const DevBox* __restrict__ boxes, const BoxRt* __restrict__ rt, unsigned char* __restrict__ work) {
   body_trace<R, LIM>(tv, blockIdx.x, boxes, rt, work);
 }
 
