@@ -1200,47 +1200,48 @@ struct TwoShock<float> {
   static constexpr int MAXIT = 20;
 };
 
-template <typename R>
-__device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R igm1, R* F) {
+template <typename R, typename M>
+__device__ __forceinline__ void two_shock_body(const R* L, const R* Rs, R gamma, R igm1, R* F, M& mul) {
+  // mul(): the products that are not an addend of a fused multiply-add
   const R rl = L[0], ul = L[1], pl = L[4];
   const R rr = Rs[0], ur = Rs[1], pr = Rs[4];
-  const R hp = R(0.5) * (gamma + R(1)), hm = R(0.5) * (gamma - R(1));
-  const R al = rl * hp, bl = rl * hm * pl;  // W_L^2 = al p + bl
-  const R ar = rr * hp, br = rr * hm * pr;
-  const R Cl = nr_sqrt(gamma * pl * rl), Cr = nr_sqrt(gamma * pr * rr);  // acoustic impedances
-  R p = (Cr * pl + Cl * pr + Cl * Cr * (ul - ur)) * nr_rcp(Cl + Cr);
+  const R hp = half_of(gamma + R(1)), hm = half_of(gamma - R(1));
+  const R al = mul(rl, hp), bl = mul(mul(rl, hm), pl);  // W_L^2 = al p + bl
+  const R ar = mul(rr, hp), br = mul(mul(rr, hm), pr);
+  const R Cl = nr_sqrt(mul(mul(gamma, pl), rl), mul), Cr = nr_sqrt(mul(mul(gamma, pr), rr), mul);  // impedances
+  R p = mul(mul(Cr, pl) + Cl * pr + mul(Cl, Cr) * (ul - ur), nr_rcp(Cl + Cr));
   p = dmax(p, R(SMALL_PRES));
   for (int it = 0; it < TwoShock<R>::MAXIT; it++) {
-    const R iwl = nr_rsqrt(al * p + bl), iwr = nr_rsqrt(ar * p + br);  // 1 / W
+    const R iwl = nr_rsqrt(al * p + bl, mul), iwr = nr_rsqrt(ar * p + br, mul);  // 1 / W
     const R dpl = p - pl, dpr = p - pr;
-    const R f = dpl * iwl + dpr * iwr + (ur - ul);
+    const R f = dpl * iwl + mul(dpr, iwr) + (ur - ul);
     // d/dp (p - p_K) / W_K = (1 - (p - p_K) (a_K / 2) / W_K^2) / W_K
-    const R dl = (R(1) - dpl * (R(0.5) * al) * iwl * iwl) * iwl;
-    const R dr = (R(1) - dpr * (R(0.5) * ar) * iwr * iwr) * iwr;
+    const R dl = mul(R(1) - mul(mul(dpl, half_of(al)), iwl) * iwl, iwl);
+    const R dr = mul(R(1) - mul(mul(dpr, half_of(ar)), iwr) * iwr, iwr);
     const R pn = dmax(p - f * nr_rcp(dl + dr), R(SMALL_PRES));
     const R step = fabs(pn - p);
     p = pn;
-    if (!dgt(step, R(TwoShock<R>::TOL) * p)) break;
+    if (!dgt(step, mul(R(TwoShock<R>::TOL), p))) break;
   }
-  const R iwl = nr_rsqrt(al * p + bl), iwr = nr_rsqrt(ar * p + br);
-  const R us = R(0.5) * ((ul - (p - pl) * iwl) + (ur + (p - pr) * iwr));
+  const R iwl = nr_rsqrt(al * p + bl, mul), iwr = nr_rsqrt(ar * p + br, mul);
+  const R us = half_of((ul - (p - pl) * iwl) + (ur + (p - pr) * iwr));
   const bool left = is_nonneg(us);
   const R rk = left ? rl : rr, uk = left ? ul : ur, pk = left ? pl : pr;
   const R vk = left ? L[2] : Rs[2], wk = left ? L[3] : Rs[3];
   const R iwk = left ? iwl : iwr, w2k = left ? al * p + bl : ar * p + br;
-  const R sgn = left ? R(1) : R(-1);  // the side's wave moves with u - sgn c
+  const R suk = left ? uk : -uk;  // the side's wave moves with u - c (left) or u + c (right)
   const R irk = nr_rcp(rk);
-  const R irs = irk - (p - pk) * iwk * iwk;  // 1 / rho*
+  const R irs = irk - mul(p - pk, iwk) * iwk;  // 1 / rho*
   // speeds of the side's wave head and tail relative to x/t = 0, positive
   // while they are on the side's own half
   R head, tail;
   if (dgt(p, pk)) {
-    head = w2k * iwk * irk - sgn * uk;  // shock: |S - u_K| = W_K / rho_K
+    head = mul(w2k, iwk) * irk - suk;  // shock: |S - u_K| = W_K / rho_K
     tail = head;
   } else {
-    const R gpk = gamma * pk * irk, gps = gamma * p * irs;
-    head = gpk * nr_rsqrt(gpk) - sgn * uk;
-    tail = gps * nr_rsqrt(gps) - sgn * us;
+    const R gpk = mul(mul(gamma, pk), irk), gps = mul(mul(gamma, p), irs);
+    head = mul(gpk, nr_rsqrt(gpk, mul)) - suk;
+    tail = mul(gps, nr_rsqrt(gps, mul)) - (left ? us : -us);
   }
   R q0, q1, q4;
   if (!is_pos(head)) {
@@ -1248,18 +1249,39 @@ __device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R ig
   } else if (is_nonneg(tail)) {
     q0 = nr_rcp(irs); q1 = us; q4 = p;    // star state
   } else {
-    const R a = head * nr_rcp(head - tail);  // x/t = 0 inside the fan
-    q0 = (R(1) - a) * rk + a * nr_rcp(irs);
-    q1 = (R(1) - a) * uk + a * us;
-    q4 = (R(1) - a) * pk + a * p;
+    const R a = mul(head, nr_rcp(head - tail));  // x/t = 0 inside the fan
+    q0 = mul(R(1) - a, rk) + a * nr_rcp(irs);
+    q1 = mul(R(1) - a, uk) + a * us;
+    q4 = mul(R(1) - a, pk) + a * p;
   }
-  const R mu = q0 * q1;
-  const R E = q4 * igm1 + R(0.5) * q0 * (q1 * q1 + vk * vk + wk * wk);
+  const R mu = mul(q0, q1);
+  const R E = mul(q4, igm1) + half_of(q0) * (mul(q1, q1) + vk * vk + wk * wk);
   F[0] = mu;
   F[1] = mu * q1 + q4;
-  F[2] = mu * vk;
-  F[3] = mu * wk;
-  F[4] = (E + q4) * q1;
+  F[2] = mul(mu, vk);
+  F[3] = mul(mu, wk);
+  F[4] = mul(E + q4, q1);
+}
+
+// FP64 products on the integer pipe, recomputed with the FP64 multiply in a
+// flagged lane, as for HLLC (IM = false: the FP64 multiply throughout).
+template <typename R, bool IM = true>
+__device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R igm1, R* F) {
+  if constexpr (!IM) {
+    PlainMul pm;
+    two_shock_body(L, Rs, gamma, igm1, F, pm);
+    return;
+  }
+  IntMul im;
+  two_shock_body(L, Rs, gamma, igm1, F, im);
+  if constexpr (Consts<R>::FP_BOUND) {
+    if (__any_sync(__activemask(), im.bad != 0u)) {
+      if (im.bad) {
+        InsnMul nm;
+        two_shock_body(L, Rs, gamma, igm1, F, nm);
+      }
+    }
+  }
 }
 
 // The handle's Riemann solver.  El, Er: total energies of the states and rsl,
@@ -1268,7 +1290,7 @@ __device__ __forceinline__ void two_shock(const R* L, const R* Rs, R gamma, R ig
 template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void riemann(const R* L, R El, R rsl, const R* Rs, R Er, R rsr, R gamma, R gm1, R igm1,
                                         R* F) {
-  if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock(L, Rs, gamma, igm1, F);
+  if constexpr (RS == HYDRO_RIEMANN_TWO_SHOCK) two_shock<R, IM>(L, Rs, gamma, igm1, F);
   else hllc<R, IM>(L, El, rsl, Rs, Er, rsr, gamma, gm1, F);
 }
 

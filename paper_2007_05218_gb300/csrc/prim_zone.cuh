@@ -5,7 +5,8 @@
 // rho is floored at SMALL_DENS, u = m / rho from one refined reciprocal,
 // p = (gamma - 1)(E - rho/2 |u|^2) floored at SMALL_PRES, and one refined
 // reciprocal square root of c^2 = gamma p / rho gives 1/c and c = c^2 (1/c).
-// gm1 = gamma - 1 (the box's stored difference, the same double).
+// gm1 = gamma - 1 (the box's stored difference, the same double).  The
+// products are formed on the integer pipe (imul_rn, bitwise __dmul_rn).
 #pragma once
 
 #include "fp64_fast.cuh"
@@ -19,25 +20,42 @@ struct PrimZone {
   double ic;  // 1 / c
 };
 
-__device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, double mz, double E,
-                                              double gamma, double gm1) {
+template <typename M>
+__device__ __forceinline__ PrimZone prim_zone_m(double rho, double mx, double my, double mz, double E, double gamma,
+                                                double gm1, M& mul) {
   // every operation written out with its rounding (fused where the product
   // feeds a sum), so that no kernel that inlines this can contract it
-  // differently from another
+  // differently from another; the products are taken by a multiplication
+  // policy (all of them correctly rounded)
   PrimZone z;
   if (dgt(SMALL_DENS, rho)) rho = SMALL_DENS;
   z.rho = rho;
   z.ir = nr_rcp(rho);
-  z.u = __dmul_rn(mx, z.ir);
-  z.v = __dmul_rn(my, z.ir);
-  z.w = __dmul_rn(mz, z.ir);
-  const double uu = __fma_rn(z.w, z.w, __fma_rn(z.v, z.v, __dmul_rn(z.u, z.u)));
-  double p = __dmul_rn(gm1, __fma_rn(__dmul_rn(-0.5, rho), uu, E));
+  z.u = mul(mx, z.ir);
+  z.v = mul(my, z.ir);
+  z.w = mul(mz, z.ir);
+  const double uu = __fma_rn(z.w, z.w, __fma_rn(z.v, z.v, mul(z.u, z.u)));
+  double p = mul(gm1, __fma_rn(-half_of(rho), uu, E));  // -rho/2 exactly
   if (dgt(SMALL_PRES, p)) p = SMALL_PRES;
   z.p = p;
-  const double c2 = __dmul_rn(__dmul_rn(gamma, p), z.ir);
-  z.ic = nr_rsqrt(c2);
-  z.cs = __dmul_rn(c2, z.ic);
+  const double c2 = mul(mul(gamma, p), z.ir);
+  z.ic = nr_rsqrt(c2, mul);
+  z.cs = mul(c2, z.ic);
+  return z;
+}
+
+// The products on the integer pipe; a warp with a flagged lane redoes that
+// lane's conversion with the FP64 multiply (the same bits).
+__device__ __forceinline__ PrimZone prim_zone(double rho, double mx, double my, double mz, double E,
+                                              double gamma, double gm1) {
+  IntMul im;
+  PrimZone z = prim_zone_m(rho, mx, my, mz, E, gamma, gm1, im);
+  if (__any_sync(__activemask(), im.bad != 0u)) {
+    if (im.bad) {
+      InsnMul nm;
+      z = prim_zone_m(rho, mx, my, mz, E, gamma, gm1, nm);
+    }
+  }
   return z;
 }
 
