@@ -46,7 +46,8 @@ namespace hydro {
 __device__ __forceinline__ double imul_rn(double a, double b, unsigned& bad) {
   const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
   const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
-  const unsigned ea = (ah >> 20) & 0x7ffu, eb = (bh >> 20) & 0x7ffu;
+  // exponent fields in place (bits 20..30 of the high words)
+  const unsigned xa = ah & 0x7ff00000u, xb = bh & 0x7ff00000u;
   const unsigned mah = (ah & 0xfffffu) | 0x100000u, mbh = (bh & 0xfffffu) | 0x100000u;
   // P = ma mb = up 2^64 + w1 2^32 + w0, up < 2^42
   const unsigned long long ll = (unsigned long long)al * bl;
@@ -57,20 +58,24 @@ __device__ __forceinline__ double imul_rn(double a, double b, unsigned& bad) {
   const unsigned uh = (unsigned)(up >> 32), ul = (unsigned)up;
   const unsigned top = (uh >> 9) & 1u;  // P >= 2^105
   const unsigned sh = 12u - top;        // the 53 kept bits end at bit 52 + top of P
-  unsigned ml = __funnelshift_l(w1, ul, sh), mh = __funnelshift_l(ul, uh, sh);
-  const unsigned rem = w1 << sh;  // the dropped bits of w1, guard bit first
-  const unsigned inc = (rem >> 31) & ((((rem & 0x7fffffffu) | w0) != 0u) | (ml & 1u));
-  const unsigned ml2 = ml + inc;
-  mh += ml2 < ml ? 1u : 0u;
-  ml = ml2;
-  const int e = (int)(ea + eb + top) - 1023;  // biased exponent of the product
+  const unsigned ml = __funnelshift_l(w1, ul, sh), mh = __funnelshift_l(ul, uh, sh);
+  // round to nearest even: the dropped bits of w1 (guard bit first; their low
+  // sh >= 11 bits are zero, so the lowest one can carry the sticky bit of w0)
+  // plus 2^31 - 1 + lsb carry out of 32 bits exactly when the kept part rounds up
+  const unsigned rem = (w1 << sh) | min(w0, 1u);
+  const unsigned inc = (unsigned)(((unsigned long long)rem + 0x7fffffffu + (ml & 1u)) >> 32);
+  const unsigned long long m = (((unsigned long long)mh << 32) | ml) + inc;
+  // result high word: exponent field (xa + xb + top - 1023, in place) plus the
+  // significand with its leading bit, which adds the one the field lacks
+  const unsigned ex = xa + xb + (top << 20) - (1024u << 20);  // (biased exponent - 1) << 20, mod 2^32
   const unsigned sign = (ah ^ bh) & 0x80000000u;
   const bool za = ((ah & 0x7fffffffu) | al) == 0u, zb = ((bh & 0x7fffffffu) | bl) == 0u;
-  const bool zero = (za & (eb < 2047u)) | (zb & (ea < 2047u));  // zero times a finite number
-  const bool ok = ((ea - 1u < 2046u) & (eb - 1u < 2046u) & ((unsigned)(e - 1) < 2046u)) | zero;
+  const bool zero = (za & (xb != 0x7ff00000u)) | (zb & (xa != 0x7ff00000u));  // zero times a finite number
+  // normal operands (field 1..2046) and a normal product (biased exponent 1..2046 before rounding)
+  const bool ok = ((xa - 0x100000u < 0x7fe00000u) & (xb - 0x100000u < 0x7fe00000u) & (ex < 0x7fe00000u)) | zero;
   bad |= ok ? 0u : 1u;
   return zero ? __hiloint2double((int)sign, 0)
-              : __hiloint2double((int)((((unsigned)(e - 1) << 20) + mh) | sign), (int)ml);
+              : __hiloint2double((int)((ex + (unsigned)(m >> 32)) | sign), (int)(unsigned)m);
 }
 
 // The FP64 multiply instruction where the integer product set `bad`: volatile,
