@@ -64,7 +64,7 @@ FLOPS_PER_UNIT = {
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
 # stands; a stage missing here has no capture of its current code and reports
 # traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553415e9 + 0.508914e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.062 GB / 12.88 M faces
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553355e9 + 0.508883e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.062 GB / 12.88 M faces
 
 
 # Compulsory HBM traffic of one zone-update in every form: the FP64 state
