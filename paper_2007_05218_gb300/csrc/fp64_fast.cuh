@@ -196,6 +196,9 @@ __device__ __forceinline__ bool dgt(R a, R b) { return dkey(a) > dkey(b); }
 // x / 2, correctly rounded
 template <typename R>
 __device__ __forceinline__ R half_of(R x) { return R(0.5) * x; }
+// 2 x, correctly rounded
+template <typename R>
+__device__ __forceinline__ R twice_of(R x) { return R(2) * x; }
 // |x| > 2 |y|
 template <typename R>
 __device__ __forceinline__ bool abs_gt_twice(R x, R y) { return fabs(x) > R(2) * fabs(y); }
@@ -264,6 +267,26 @@ __device__ __forceinline__ double half_of<double>(double x) {
   const unsigned rh = (qh + (rl < ql ? 1u : 0u)) | ((unsigned)hi & 0x80000000u);
   const unsigned oh = dec ? (unsigned)hi - (1u << 20) : keep ? (unsigned)hi : rh;
   return __hiloint2double((int)oh, (int)(dec | keep ? lo : rl));
+}
+// 2 x without an FP64 instruction: an exponent increment of the high word for
+// 2^-1022 <= |x| < 2^1023, the magnitude pattern doubled for |x| below that
+// (exact, also where it becomes normal), infinity of x's sign for
+// 2^1023 <= |x| < inf; infinities and NaN are returned unchanged.
+template <>
+__device__ __forceinline__ double twice_of<double>(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned mh = hi & 0x7fffffffu, sign = hi & 0x80000000u;
+  const bool sub = mh < 0x00100000u, big = mh >= 0x7fe00000u, special = mh >= 0x7ff00000u;
+  unsigned rh = hi + 0x00100000u, rl = lo;
+  if (sub) {
+    rh = ((mh << 1) | (lo >> 31)) | sign;
+    rl = lo << 1;
+  }
+  if (big) {
+    rh = special ? hi : (sign | 0x7ff00000u);
+    rl = special ? lo : 0u;
+  }
+  return __hiloint2double((int)rh, (int)rl);
 }
 // |x| > 2 |y| for finite x, y, on the magnitude bits: 2|y| is an exponent
 // increment of a normal |y| and the magnitude pattern doubled for a

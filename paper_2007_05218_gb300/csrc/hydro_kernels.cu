@@ -460,6 +460,12 @@ __device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double ie_div(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float ie_div(float a, float b) { return __fdiv_rn(a, b); }
+// a single rounded product by a multiplication policy: the policy's FP64
+// product (correctly rounded, never fused), the FP32 intrinsic
+template <typename M>
+__device__ __forceinline__ double ie_mul(double a, double b, M& mul) { return mul(a, b); }
+template <typename M>
+__device__ __forceinline__ float ie_mul(float a, float b, M&) { return __fmul_rn(a, b); }
 
 // ---------------------------------------------------------------- flattening
 // CW84's shock test |dp1| / min(p) > eps, a discontinuous decision.  FP64: the
@@ -646,20 +652,20 @@ __device__ __forceinline__ void slopes_zone(const DevBox& b, R* __restrict__ W, 
 constexpr double CS_C = 1.25;
 
 
-// second difference a - 2 b + c, as (a - 2 b) + c
+// second difference a - 2 b + c, as (a - 2 b) + c (the doubling exact)
 template <typename R>
-__device__ __forceinline__ R ie_d2(R a, R b, R c) { return ie_add(ie_sub(a, ie_mul(R(2), b)), c); }
+__device__ __forceinline__ R ie_d2(R a, R b, R c) { return ie_add(ie_sub(a, twice_of(b)), c); }
 
 // CS08's limited second difference: when d2 and the neighbouring second
 // differences o[] all share a sign, the smallest of |d2| and C |o|, with the
 // sign of d2; else zero.
-template <typename R, int NO>
-__device__ __forceinline__ R cs_limited_d2(R d2, const R* o) {
+template <typename R, int NO, typename M>
+__device__ __forceinline__ R cs_limited_d2(R d2, const R* o, M& mul) {
   R m = fabs(d2);
 #pragma unroll
   for (int k = 0; k < NO; k++) {
     if (!same_sign(d2, o[k])) return R(0);
-    m = dmin(m, ie_mul(R(CS_C), fabs(o[k])));
+    m = dmin(m, ie_mul(R(CS_C), fabs(o[k]), mul));
   }
   return copysign(m, d2);
 }
@@ -669,13 +675,13 @@ __device__ __forceinline__ R cs_limited_d2(R d2, const R* o) {
 // (a0 + a1)/2 - d2_lim/6 from the limited second difference d2 = 3 (a0 - 2v + a1)
 // when it does not lie between a0 and a1 (CS08 §2.1; the division by 6 is a
 // correctly rounded divide, taken only on that branch).
-template <typename R>
-__device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
-  R v = ie_sub(ie_mul(R(7.0 / 12.0), ie_add(a0, a1)), ie_mul(R(1.0 / 12.0), ie_add(am, a2)));
+template <typename R, typename M>
+__device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2, M& mul) {
+  R v = ie_sub(ie_mul(R(7.0 / 12.0), ie_add(a0, a1), mul), ie_mul(R(1.0 / 12.0), ie_add(am, a2), mul));
   if (opp_sign(ie_sub(v, a0), ie_sub(a1, v))) {
-    const R d2 = ie_mul(R(3), ie_add(ie_sub(a0, ie_mul(R(2), v)), a1));
+    const R d2 = ie_mul(R(3), ie_add(ie_sub(a0, twice_of(v)), a1), mul);
     const R o[2] = {ie_d2(am, a0, a1), ie_d2(a0, a1, a2)};
-    v = ie_sub(ie_mul(R(0.5), ie_add(a0, a1)), ie_div(cs_limited_d2<R, 2>(d2, o), R(6)));
+    v = ie_sub(half_of(ie_add(a0, a1)), ie_div(cs_limited_d2<R, 2>(d2, o, mul), R(6)));
   }
   return v;
 }
@@ -683,14 +689,32 @@ __device__ __forceinline__ R cs_interface(R am, R a0, R a1, R a2) {
 // Interface values of the five normal-frame variables of axis D at the low
 // face of each zone of [-2, n_D+1] along D and [-1, n] across it (stored in
 // the slope fields, which CS08 does not use).
+// (FP64: the products on the integer pipe, the five interfaces redone with
+// the FP64 multiply in a lane that flagged -- the same bits)
 template <typename R, int D>
 __device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W, long long Z) {
   const long long vs = b.vs, s = b.s[D];
+  R v[5];
+  IntMul im;
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const R* a = W + comp<D>(m) * vs + Z;
-    W[(FLD_DQ + 5 * D + m) * vs + Z] = cs_interface(a[-2 * s], a[-s], a[0], a[s]);
+    v[m] = cs_interface(a[-2 * s], a[-s], a[0], a[s], im);
   }
+  if constexpr (Consts<R>::FP_BOUND) {
+    if (__any_sync(__activemask(), im.bad != 0u)) {
+      if (im.bad) {
+        InsnMul nm;
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+          const R* a = W + comp<D>(m) * vs + Z;
+          v[m] = cs_interface(a[-2 * s], a[-s], a[0], a[s], nm);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 5; m++) W[(FLD_DQ + 5 * D + m) * vs + Z] = v[m];
 }
 
 // Parabola of zone value a0 (neighbours amm, am, ap, app) between the
@@ -701,13 +725,13 @@ __device__ __forceinline__ void cs_faces_zone(const DevBox& b, R* __restrict__ W
 // with single IEEE operations, as for cs_interface; the edge values the
 // branches then produce feed only continuous stages and take the fast path
 // (approximate reciprocal, fused multiply-adds).
-template <typename R, bool BLEND = true>
-__device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt) {
+template <typename R, bool BLEND = true, typename M>
+__device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f, R& L, R& Rt, M& mul) {
   const R dL = ie_sub(L, a0), dR = ie_sub(Rt, a0);
   if (!same_sign(dR, ie_sub(a0, L)) || !same_sign(ie_sub(ap, a0), ie_sub(a0, am))) {
-    const R d2 = ie_mul(R(6), ie_sub(ie_add(L, Rt), ie_mul(R(2), a0)));
+    const R d2 = ie_mul(R(6), ie_sub(ie_add(L, Rt), twice_of(a0)), mul);
     const R o[3] = {ie_d2(amm, am, a0), ie_d2(am, a0, ap), ie_d2(a0, ap, app)};
-    const R lim = cs_limited_d2<R, 3>(d2, o);
+    const R lim = cs_limited_d2<R, 3>(d2, o, mul);
     if (is_pos(fabs(lim))) {
       // lim / d2 in (0, 1]; a true divide when d2 is too small for the
       // approximate reciprocal (subnormal range)
@@ -718,9 +742,9 @@ __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f,
       L = a0;
       Rt = a0;
     }
-  } else if (!dgt(ie_mul(R(2), fabs(dL)), fabs(dR))) {
+  } else if (!dgt(twice_of(fabs(dL)), fabs(dR))) {
     Rt = a0 - R(2) * dL;
-  } else if (!dgt(ie_mul(R(2), fabs(dR)), fabs(dL))) {
+  } else if (!dgt(twice_of(fabs(dR)), fabs(dL))) {
     L = a0 - R(2) * dR;
   }
   if (BLEND && is_pos(f)) {
@@ -965,9 +989,9 @@ __device__ __forceinline__ void trace_edges(const R* a0, const R* aL, const R* a
 
 // The limited parabolas (edges aL, aR) of the five normal-frame variables
 // of zone Z along D, flattened by f when BLEND.
-template <typename R, int D, int LIM, bool BLEND>
-__device__ __forceinline__ void zone_parabolas(const R* __restrict__ W, long long vs, long long s, long long Z, R f,
-                                               R* a0, R* aL, R* aR) {
+template <typename R, int D, int LIM, bool BLEND, typename M>
+__device__ __forceinline__ void zone_parabolas_m(const R* __restrict__ W, long long vs, long long s, long long Z, R f,
+                                                 R* a0, R* aL, R* aR, M& mul) {
 #pragma unroll
   for (int m = 0; m < 5; m++) {
     const R* a = W + comp<D>(m) * vs + Z;
@@ -976,9 +1000,26 @@ __device__ __forceinline__ void zone_parabolas(const R* __restrict__ W, long lon
     if constexpr (LIM == HYDRO_LIMITER_CS08) {
       aL[m] = dq[0];
       aR[m] = dq[s];
-      cs_parabola<R, BLEND>(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m]);
+      cs_parabola<R, BLEND>(a[-2 * s], a[-s], a[0], a[s], a[2 * s], f, aL[m], aR[m], mul);
     } else {
       parabola<R, BLEND>(a[-s], a[0], a[s], dq[-s], dq[0], dq[s], f, aL[m], aR[m]);
+    }
+  }
+}
+
+// (FP64 CS08: the limiter's products on the integer pipe, the five parabolas
+// redone with the FP64 multiply in a lane that flagged -- the same bits)
+template <typename R, int D, int LIM, bool BLEND>
+__device__ __forceinline__ void zone_parabolas(const R* __restrict__ W, long long vs, long long s, long long Z, R f,
+                                               R* a0, R* aL, R* aR) {
+  IntMul im;
+  zone_parabolas_m<R, D, LIM, BLEND>(W, vs, s, Z, f, a0, aL, aR, im);
+  if constexpr (Consts<R>::FP_BOUND && LIM == HYDRO_LIMITER_CS08) {
+    if (__any_sync(__activemask(), im.bad != 0u)) {
+      if (im.bad) {
+        InsnMul nm;
+        zone_parabolas_m<R, D, LIM, BLEND>(W, vs, s, Z, f, a0, aL, aR, nm);
+      }
     }
   }
 }

@@ -1,6 +1,6 @@
 // Checks the device arithmetic helpers of fp64_fast.cuh on the GPU against
 // IEEE operations: the bit-pattern sign tests, comparisons, min/max, exact
-// halving, the |x| > 2|y| test, the integer FP64 -> FP32 rounding (against
+// halving and doubling, the |x| > 2|y| test, the integer FP64 -> FP32 rounding (against
 // the conversion instruction, where it does not defer to it) and the
 // integer-pipe product (against the FP64 multiply) bit for bit, on
 // patterns drawn over every
@@ -31,6 +31,8 @@ __global__ void check_bits(const double* x, const double* y, int n, unsigned lon
   const double a = x[i], c = y[i];
   const double h = half_of<double>(a), r = __dmul_rn(0.5, a);
   if (!(__double_as_longlong(h) == __double_as_longlong(r) || (isnan(h) && isnan(r)))) atomicAdd(&bad[BAD_HALF], 1ull);
+  const double w = twice_of<double>(a), v2 = __dmul_rn(2.0, a);
+  if (!(__double_as_longlong(w) == __double_as_longlong(v2) || (isnan(w) && isnan(v2)))) atomicAdd(&bad[BAD_HALF], 1ull);
   {  // the integer-pipe product: bitwise the IEEE one wherever it does not
      // defer, and deferring exactly where an operand is subnormal, infinite
      // or NaN (zero excepted) or the product is not normal or zero
@@ -219,7 +221,7 @@ int main() {
   cudaMemcpy(bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost);
   cudaMemcpy(worst, dworst, sizeof(worst), cudaMemcpyDeviceToHost);
   std::printf("cuda %s\n", cudaGetErrorString(err));
-  std::printf("bit-pattern cases %d: half_of mismatches %llu, comparison mismatches %llu, narrowing mismatches %llu, "
+  std::printf("bit-pattern cases %d: half_of / twice_of mismatches %llu, comparison mismatches %llu, narrowing mismatches %llu, "
               "integer-product mismatches %llu\n",
               n, bad[BAD_HALF], bad[BAD_CMP], bad[BAD_NARROW], bad[BAD_IMUL]);
   std::printf("refined cases %d: rcp > 2 ulp %llu (max %.3f), sqrt > 2 ulp %llu (max %.3f), rsqrt > 2^-51.5 %llu "

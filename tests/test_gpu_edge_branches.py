@@ -13,6 +13,9 @@
   and each test asserts that its branch was taken there.  FP64 against the
   oracle at 1e-10 relative L-inf after 10 steps; mixed precision at 1e-5
   relative L1 in rho and E.
+- A subnormal momentum, which sends the integer-pipe FP64 products that read
+  it to the recomputation with the FP64 multiply, with either Riemann
+  solver.
 """
 import numpy as np
 import pytest
@@ -114,3 +117,25 @@ def test_mixed_matches_oracle_on_guard_branches(name):
     err_rho, err_E = rel_l1(Um[0], Uo[0]), rel_l1(Um[4], Uo[4])
     print(f"{name}: rel L1 rho {err_rho:.3e}, E {err_E:.3e}")
     assert err_rho <= TOL_L1 and err_E <= TOL_L1, (err_rho, err_E)
+
+
+@pytest.mark.parametrize("riemann", [hydro.HYDRO_RIEMANN_HLLC, hydro.HYDRO_RIEMANN_TWO_SHOCK])
+def test_subnormal_momentum_takes_the_fp64_multiply_recomputation(riemann):
+    # A transverse velocity of 1e-310 makes that momentum subnormal: every
+    # integer-pipe product that reads it (the primitive conversion's m / rho,
+    # the conserved form of each traced state, the corrections' velocities,
+    # the Riemann solvers' transverse fluxes) defers, and the warps redo those
+    # units with the FP64 multiply.  The result must still match the oracle.
+    pr = inputs.density_wave((24, 20, 16), seed=2, vel=(1.0, 0.5, 1e-310))
+    assert 0.0 < np.max(np.abs(pr.U[3])) < 2.2250738585072014e-308  # subnormal
+    Uo, to, _, rc = oracle.run(pr, nsteps=10, nthreads=8, riemann=riemann)
+    assert rc == 0
+    B = hydro.Boxes([pr], riemann=riemann)
+    B.step(10)
+    B.sync()
+    U, t = B.interior(0), B.time()[0]
+    B.close()
+    err = rel_linf(U, Uo)
+    print("rel L-inf per field", err)
+    assert np.all(err <= TOL), err
+    assert t == pytest.approx(to, rel=1e-12)
