@@ -119,7 +119,7 @@ enum TableId : int {
   TB_TILE,       // fused tile stage: tracing, CTU, solves and update per z-marching tile (FP32 boxes)
   NTABLES
 };
-constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 1, 2, 3, 6, 1};
+constexpr int TABLE_ZDIM[NTABLES] = {1, 1, 1, 1, 1, 1, 3, 3, 3, 6, 3, 1, 2, 3, 6, 1};
 // tables of the precision-specific stage kernels exist once per compute type
 constexpr bool TABLE_PER_PRECISION[NTABLES] = {false, false, false, false, false, true, true, true, true, true, true,
                                                true, true, true, true, true};

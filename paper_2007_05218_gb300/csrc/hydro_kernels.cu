@@ -1531,53 +1531,41 @@ __device__ __forceinline__ void ctu1_pair(const DevBox& b, R* __restrict__ W, lo
   store_flux<R, D>(W + (FLD_F1 + 5 * pair_slot(D, T)) * vs, vs, Z, Fn);
 }
 
-// FP32: the two states stay in registers for both pairs.  FP64: each pair
-// loads them (the second load hits L1), so that 18 doubles are not held
-// across a Riemann solve -- registers, not HBM, limit the FP64 kernel.
-template <typename R, int D, int RS, bool IM = true>
-__device__ __forceinline__ void ctu1_face(const DevBox& b, R* __restrict__ W, long long Z, const BoxRt& rt,
-                                          bool with_e, bool with_f) {
-  constexpr int E = (D + 1) % 3, F = (D + 2) % 3;
+// One thread per D-face and transverse axis T (the ordered pair (D, T), work
+// item z = its pair slot): faces [0, n_D] along D, [0, n_T) along T and
+// [-1, n] along the remaining axis.  (Both pairs of a face in one thread load
+// its two states once, but with the products on the integer pipe the kernel
+// is bound by latency rather than by its loads: one pair per thread, more
+// threads with fewer registers, measured 3.6 % faster.)
+template <typename R, int D, int T, int RS, bool IM>
+__device__ __forceinline__ void ctu1_one_pair(const DevBox& b, R* __restrict__ W, long long t, const BoxRt& rt) {
+  constexpr int U = 3 - D - T;
+  int lo[3], ext[3], c[3];
+  lo[D] = 0;
+  ext[D] = b.n[D] + 1;
+  lo[T] = 0;
+  ext[T] = b.n[T];
+  lo[U] = -1;
+  ext[U] = b.n[U] + 2;
+  if (!decode(t, lo, ext, c)) return;
+  const long long Z = zone(b, c[0], c[1], c[2]);
   R qL[5], qR[5], uL[4], uR[4];
-  if constexpr (Consts<R>::STORE_CONSERVED) {
-    if (with_e) {
-      load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-      ctu1_pair<R, D, E, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
-    }
-    if (with_f) {
-      load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-      ctu1_pair<R, D, F, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
-    }
-  } else {
-    load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
-    if (with_e) ctu1_pair<R, D, E, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
-    if (with_f) ctu1_pair<R, D, F, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
-  }
+  load_face_states<R, D>(W, b.vs, Z, b.s[D], Consts<R>::igm1(b), qL, uL, qR, uR);
+  ctu1_pair<R, D, T, RS, IM>(b, W, Z, rt, qL, uL, qR, uR);
 }
-
-// One thread per D-face over faces [0, n_D] along D and [-1, n] across it:
-// pair (D, E) is defined where the E index is in [0, n_E - 1], pair (D, F)
-// where the F index is in [0, n_F - 1] (E = D+1, F = D+2 mod 3).
 template <typename R, int RS, bool IM = true>
 __device__ __forceinline__ void body_ctu1(const TableView& tv, const int blk_, const DevBox* boxes, const BoxRt* rt, unsigned char* work) {
   LOCATE_AT(tv, blk_)
   if (!box_uses<R>(b)) return;
-  const int d = z_;
-  const int e = (d + 1) % 3, f = (d + 2) % 3;
-  int lo[3] = {-1, -1, -1}, ext[3] = {b.n[0] + 2, b.n[1] + 2, b.n[2] + 2}, c[3];
-  lo[d] = 0;
-  ext[d] = b.n[d] + 1;
-  if (!decode(t_, lo, ext, c)) return;
-  const bool with_e = c[e] >= 0 && c[e] < b.n[e];
-  const bool with_f = c[f] >= 0 && c[f] < b.n[f];
-  if (!with_e && !with_f) return;
-  const long long Z = zone(b, c[0], c[1], c[2]);
   R* W = fields<R>(work, b);
   const BoxRt& rtb = rt[bi];
-  switch (d) {
-    case 0: ctu1_face<R, 0, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
-    case 1: ctu1_face<R, 1, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
-    default: ctu1_face<R, 2, RS, IM>(b, W, Z, rtb, with_e, with_f); break;
+  switch (z_) {
+    case 0: ctu1_one_pair<R, 0, 1, RS, IM>(b, W, t_, rtb); break;
+    case 1: ctu1_one_pair<R, 0, 2, RS, IM>(b, W, t_, rtb); break;
+    case 2: ctu1_one_pair<R, 1, 0, RS, IM>(b, W, t_, rtb); break;
+    case 3: ctu1_one_pair<R, 1, 2, RS, IM>(b, W, t_, rtb); break;
+    case 4: ctu1_one_pair<R, 2, 0, RS, IM>(b, W, t_, rtb); break;
+    default: ctu1_one_pair<R, 2, 1, RS, IM>(b, W, t_, rtb); break;
   }
 }
 
@@ -2966,7 +2954,10 @@ long long item_volume(const hydro_box_desc& d, int table, int z) {
     case TB_TRACE: return (n[0] + 2) * (n[1] + 2) * (n[2] + 2);
     case TB_SLOPES: return (n[z] + 4) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
     case TB_RIEMANN: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
-    case TB_CTU1: return (n[z] + 1) * (n[(z + 1) % 3] + 2) * (n[(z + 2) % 3] + 2);
+    case TB_CTU1: {  // z = pair slot of (D, T)
+      const int dd = z / 2, r = z % 2, tt = r < dd ? r : r + 1, uu = 3 - dd - tt;
+      return (n[dd] + 1) * n[tt] * (n[uu] + 2);
+    }
     case TB_CTU2: return (n[z] + 1) * n[(z + 1) % 3] * n[(z + 2) % 3];
     case TB_LINE_X: return (n[1] + 2) * (n[2] + 2) * ((n[0] + 2 + LINE_X_OUT - 1) / LINE_X_OUT) * 32;
     case TB_LINE_YZ: {
