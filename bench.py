@@ -64,7 +64,13 @@ FLOPS_PER_UNIT = {
 # DRAM bytes (read + write) per unit from one ncu capture of the kernel as it
 # stands; a stage missing here has no capture of its current code and reports
 # traffic null.
-TRAFFIC_BYTES_PER_UNIT = {"ctu1": (1.553355e9 + 0.508883e9) / 12879360}  # k_ctu1<double, 0>, 128^3 capture: 2.062 GB / 12.88 M faces
+TRAFFIC_BYTES_PER_UNIT = {"ctu1": (19.339838e9 + 4.109397e9) / 101846016}  # k_ctu1<double, 0>, 256^3 capture: 23.45 GB / 101.8 M faces
+
+# FP64-pipe warp-instruction slots per unit (x 32 lanes) from the same capture.
+# With the products on the integer pipe, the FP64 pipe's ceiling for the
+# kernel's own mix is its peak x (algorithmic flops per unit) / (2 x slots per
+# unit): the rate at which the kernel would run with that pipe always busy.
+FP64_SLOTS_PER_UNIT = {"ctu1": 83.0}
 
 
 # Compulsory HBM traffic of one zone-update in every form: the FP64 state
@@ -725,9 +731,15 @@ def main() -> None:
                 "traffic": (TRAFFIC_BYTES_PER_UNIT[top] * units_per_launch(top, n)
                             if top in TRAFFIC_BYTES_PER_UNIT else None),
                 "peak_source": "derived from unit counts and clocks: 152 SMs x 4 FP64 flop/clk/SM x 2070 MHz",
-                "note": ("the kernel forms its FP64 products (45 of the 129 FP64 operations of a corrected face) "
+                "note": ("the kernel forms its FP64 products (45 of the 128 FP64 operations of a corrected face) "
                          "on the integer pipe, bitwise the FP64 multiply; achieved counts all of its algorithmic "
-                         "flops against the FP64 pipe's peak, so frac can pass what that pipe alone delivers"),
+                         "flops against the FP64 pipe's peak, so frac can pass what that pipe alone delivers; "
+                         "mix_ceiling is that pipe's peak for the kernel's own FP64 instruction mix"),
+                "mix_ceiling": (FP64_NOMINAL_FLOPS * FLOPS_PER_UNIT[top] / (2.0 * FP64_SLOTS_PER_UNIT[top]) / 1e12
+                                if top in FP64_SLOTS_PER_UNIT else None),
+                "frac_of_mix_ceiling": (achieved / (FP64_NOMINAL_FLOPS * FLOPS_PER_UNIT[top] / (2.0 * FP64_SLOTS_PER_UNIT[top]))
+                                        if top in FP64_SLOTS_PER_UNIT else None),
+                "fp64_slots_per_unit": FP64_SLOTS_PER_UNIT.get(top),
                 "peak_measured": fp64_probe / 1e12, "frac_of_measured": achieved / fp64_probe,
                 "peak_measured_source": "FP64 multiply-add probe on every SM (hydro_measure_peaks), this run",
                 "kernel_time_source": f"events around each stage launch, {nprof} profiled steps after the timed region",
