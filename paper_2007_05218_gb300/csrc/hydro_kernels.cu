@@ -748,8 +748,8 @@ __device__ __forceinline__ void cs_parabola(R amm, R am, R a0, R ap, R app, R f,
     L = a0 - R(2) * dR;
   }
   if (BLEND && is_pos(f)) {
-    L = f * a0 + (R(1) - f) * L;
-    Rt = f * a0 + (R(1) - f) * Rt;
+    L = fma(f, a0, (R(1) - f) * L);
+    Rt = fma(f, a0, (R(1) - f) * Rt);
   }
 }
 
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256) k_slopes(TableView tv, const DevBox* __re
 // halving exact (on the integer pipe in FP64).
 template <typename R>
 __device__ __forceinline__ R ppm_face(R am1, R a0, R dm1, R d0) {
-  return half_of(am1 + a0) - (d0 - dm1) * R(1.0 / 6.0);
+  return fma(dm1 - d0, R(1.0 / 6.0), half_of(am1 + a0));
 }
 
 // CW84 monotonicity limiter of the parabola of zone value a0 between face
@@ -827,8 +827,8 @@ __device__ __forceinline__ void cw84_limit(R a0, R f, R& L, R& Rt) {
     Rt = a0 + R(2) * x;
   }
   if (BLEND && is_pos(f)) {
-    L = f * a0 + (R(1) - f) * L;
-    Rt = f * a0 + (R(1) - f) * Rt;
+    L = fma(f, a0, (R(1) - f) * L);
+    Rt = fma(f, a0, (R(1) - f) * Rt);
   }
 }
 
@@ -846,7 +846,7 @@ __device__ __forceinline__ void conserved_m(const R* q, R igm1, R* u, M& mul) {
   u[0] = mul(q[0], q[1]);
   u[1] = mul(q[0], q[2]);
   u[2] = mul(q[0], q[3]);
-  u[3] = mul(q[4], igm1) + half_of(q[0]) * (mul(q[1], q[1]) + q[2] * q[2] + q[3] * q[3]);
+  u[3] = fma(half_of(q[0]), fma(q[3], q[3], fma(q[2], q[2], mul(q[1], q[1]))), mul(q[4], igm1));
 }
 
 // Conserved momenta (normal frame) and total energy of a traced edge state,
@@ -895,33 +895,33 @@ __device__ __forceinline__ void trace_side(const R* a0, const R* aL, const R* aR
   if constexpr (SIDE == 1) {
     // right edge: waves with lambda > 0; the fastest (u+c) supplies the reference state
     if (is_pos(lp)) {
-      R h1 = mul(lp, hdt), h2 = R(6) - lp * fdt;
+      R h1 = mul(lp, hdt), h2 = fma(-lp, fdt, R(6));
       R ref[5];
 #pragma unroll
-      for (int m = 0; m < 5; m++) ref[m] = aR[m] - h1 * (dA[m] - h2 * c6[m]);
+      for (int m = 0; m < 5; m++) ref[m] = fma(-h1, fma(-h2, c6[m], dA[m]), aR[m]);
       R bm = R(0), b0 = R(0);
       out[2] = ref[2];
       out[3] = ref[3];
       const bool wm = is_pos(lm), w0 = is_pos(u);
       if (any_in_warp<R>(wm)) {
-        h1 = mul(lm, hdt); h2 = R(6) - lm * fdt;
-        const R du = ref[1] - (aR[1] - h1 * (dA[1] - h2 * c6[1]));
-        const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
-        if (wm) bm = mul(-rc, du) + i2c2 * dp;
+        h1 = mul(lm, hdt); h2 = fma(-lm, fdt, R(6));
+        const R du = ref[1] - fma(-h1, fma(-h2, c6[1], dA[1]), aR[1]);
+        const R dp = ref[4] - fma(-h1, fma(-h2, c6[4], dA[4]), aR[4]);
+        if (wm) bm = fma(i2c2, dp, mul(-rc, du));
       }
       if (any_in_warp<R>(w0)) {
-        h1 = mul(u, hdt); h2 = R(6) - u * fdt;
-        const R dr = ref[0] - (aR[0] - h1 * (dA[0] - h2 * c6[0]));
-        const R dp = ref[4] - (aR[4] - h1 * (dA[4] - h2 * c6[4]));
+        h1 = mul(u, hdt); h2 = fma(-u, fdt, R(6));
+        const R dr = ref[0] - fma(-h1, fma(-h2, c6[0], dA[0]), aR[0]);
+        const R dp = ref[4] - fma(-h1, fma(-h2, c6[4], dA[4]), aR[4]);
         if (w0) {
-          b0 = dr - ic2 * dp;
-          out[2] = aR[2] - h1 * (dA[2] - h2 * c6[2]);
-          out[3] = aR[3] - h1 * (dA[3] - h2 * c6[3]);
+          b0 = fma(-ic2, dp, dr);
+          out[2] = fma(-h1, fma(-h2, c6[2], dA[2]), aR[2]);
+          out[3] = fma(-h1, fma(-h2, c6[3], dA[3]), aR[3]);
         }
       }
       out[0] = ref[0] - (bm + b0);
-      out[1] = ref[1] + cr * bm;
-      out[4] = ref[4] - c2 * bm;
+      out[1] = fma(cr, bm, ref[1]);
+      out[4] = fma(-c2, bm, ref[4]);
     } else {
 #pragma unroll
       for (int m = 0; m < 5; m++) out[m] = a0[m];
@@ -931,33 +931,33 @@ __device__ __forceinline__ void trace_side(const R* a0, const R* aL, const R* aR
   } else {
     // left edge: waves with lambda < 0; the fastest (u-c) supplies the reference state
     if (is_neg(lm)) {
-      R h1 = mul(-lm, hdt), h2 = R(6) + lm * fdt;
+      R h1 = mul(-lm, hdt), h2 = fma(lm, fdt, R(6));
       R ref[5];
 #pragma unroll
-      for (int m = 0; m < 5; m++) ref[m] = aL[m] + h1 * (dA[m] + h2 * c6[m]);
+      for (int m = 0; m < 5; m++) ref[m] = fma(h1, fma(h2, c6[m], dA[m]), aL[m]);
       R bp = R(0), b0 = R(0);
       out[2] = ref[2];
       out[3] = ref[3];
       const bool wp = is_neg(lp), w0 = is_neg(u);
       if (any_in_warp<R>(wp)) {
-        h1 = mul(-lp, hdt); h2 = R(6) + lp * fdt;
-        const R du = ref[1] - (aL[1] + h1 * (dA[1] + h2 * c6[1]));
-        const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
-        if (wp) bp = mul(rc, du) + i2c2 * dp;
+        h1 = mul(-lp, hdt); h2 = fma(lp, fdt, R(6));
+        const R du = ref[1] - fma(h1, fma(h2, c6[1], dA[1]), aL[1]);
+        const R dp = ref[4] - fma(h1, fma(h2, c6[4], dA[4]), aL[4]);
+        if (wp) bp = fma(i2c2, dp, mul(rc, du));
       }
       if (any_in_warp<R>(w0)) {
-        h1 = mul(-u, hdt); h2 = R(6) + u * fdt;
-        const R dr = ref[0] - (aL[0] + h1 * (dA[0] + h2 * c6[0]));
-        const R dp = ref[4] - (aL[4] + h1 * (dA[4] + h2 * c6[4]));
+        h1 = mul(-u, hdt); h2 = fma(u, fdt, R(6));
+        const R dr = ref[0] - fma(h1, fma(h2, c6[0], dA[0]), aL[0]);
+        const R dp = ref[4] - fma(h1, fma(h2, c6[4], dA[4]), aL[4]);
         if (w0) {
-          b0 = dr - ic2 * dp;
-          out[2] = aL[2] + h1 * (dA[2] + h2 * c6[2]);
-          out[3] = aL[3] + h1 * (dA[3] + h2 * c6[3]);
+          b0 = fma(-ic2, dp, dr);
+          out[2] = fma(h1, fma(h2, c6[2], dA[2]), aL[2]);
+          out[3] = fma(h1, fma(h2, c6[3], dA[3]), aL[3]);
         }
       }
       out[0] = ref[0] - (b0 + bp);
-      out[1] = ref[1] - cr * bp;
-      out[4] = ref[4] - c2 * bp;
+      out[1] = fma(-cr, bp, ref[1]);
+      out[4] = fma(-c2, bp, ref[4]);
     } else {
 #pragma unroll
       for (int m = 0; m < 5; m++) out[m] = a0[m];
