@@ -866,7 +866,12 @@ __device__ __forceinline__ void store_conserved(R* __restrict__ W, long long vs,
 // with ic = 1/c and cr = c/rho, dt/dx.  trace_side<1> forms the right-edge
 // state (the left state of the zone's high face), trace_side<0> the
 // left-edge state, with the products that are not an addend of a fused
-// multiply-add taken by a multiplication policy.
+// multiply-add taken by a multiplication policy.  Every product is written
+// either as a policy multiply or as an explicit fma(), so that the compiler
+// has no multiply-add to fuse by choice: the per-stage kernel and the
+// persistent kernel's copy of this body then round alike (with products left
+// to contraction, the two copies differed by an ulp in a few zones of a long
+// Sedov run).
 //
 // The parabola's dA = aR - aL and a6 = 6 (a0 - (aL + aR)/2) (CW84 §1); the
 // factor 6 of a6 is carried by h2 below, so c6 holds a6 / 6.  For a wave of
