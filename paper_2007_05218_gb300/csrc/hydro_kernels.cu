@@ -454,10 +454,8 @@ __global__ void __launch_bounds__(256) k_dt_shared(const DevBox* __restrict__ bo
 // bitwise equal decisions on any IEEE machine.
 __device__ __forceinline__ double ie_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ie_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double ie_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float ie_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float ie_sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float ie_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double ie_div(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float ie_div(float a, float b) { return __fdiv_rn(a, b); }
 // a single rounded product by a multiplication policy: the policy's FP64
